@@ -1,0 +1,337 @@
+"""Throughput of the split-step Crank-Nicolson path on one GB300 (or N replicas).
+
+One bench step = ``--inner`` imaginary-time split steps (H1 + x/y[/z] CN
+sweeps + norm, every row of the hot path) followed by one evaluation of the
+observables and the vortex count, on the synthetic workload named by
+``--workload`` (default: 3D 256 x 256 x 128, complex FP32 with FP64
+reductions, seeded one-vortex random-phase start).  The metric is split-step
+site-updates per second: stored grid sites x split steps / device time.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle instead (on this host's cores, one bounded split step per bench step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "split-step CN site-updates/s"
+UNIT = "site-updates/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="3d-256x256x128-fp32")
+    p.add_argument("--inner", type=int, default=100, help="split steps per bench step")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--skip-baselines", action="store_true",
+                   help="no e2e and no CPU baseline (profiling runs)")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel
+    source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        rec = d["kernels"][kernel]
+        src = os.path.join(ROOT, "paper_1906_06327_gb300", "csrc", rec["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if h != rec["source_sha256"]:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        if not shutil.which("nvidia-smi"):
+            return
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = subprocess.Popen(
+            ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader",
+             "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1].split()[0]))
+                smax = float(r[2].split()[0])
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (IndexError, ValueError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(name):
+    from paper_1906_06327_gb300 import inputs
+    if name not in inputs.WORKLOADS:
+        raise SystemExit(f"unknown workload {name}; choose from {sorted(inputs.WORKLOADS)}")
+    return inputs.WORKLOADS[name]
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _cpu_oracle_rate(w, seconds_budget: float, max_steps: int | None = None):
+    """Time the FP64 oracle (one thread) on split steps of the same workload."""
+    import oracle
+    from paper_1906_06327_gb300 import inputs
+    grid = oracle.Grid(w.n, w.h)
+    phys = oracle.Phys(gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt)
+    psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(w.n[0], w.n[1], w.seed))
+    steps, total = 0, 0.0
+    while True:
+        t0 = time.perf_counter()
+        psi, _ = oracle.steps(grid, phys, psi, 1, True)
+        total += time.perf_counter() - t0
+        steps += 1
+        if total >= seconds_budget or (max_steps and steps >= max_steps):
+            break
+    return w.sites * steps / total, steps, total
+
+
+def run_reference(a, w):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from paper_1906_06327_gb300 import inputs
+    grid = oracle.Grid(w.n, w.h)
+    phys = oracle.Phys(gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt)
+    psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(w.n[0], w.n[1], w.seed))
+    for _ in range(a.warmup):
+        psi, _ = oracle.steps(grid, phys, psi, 1, True)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        psi, _ = oracle.steps(grid, phys, psi, 1, True)
+    dt = time.perf_counter() - t0
+    value = w.sites * a.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "grid": list(w.n), "spacing": list(w.h),
+                   "step": "1 imaginary-time split step per bench step (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{a.steps} imaginary-time split steps of the {w.name} grid, "
+                                   "FP64 C oracle, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU path
+def run_ours(a, w):
+    import numpy as np
+    import torch
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1906_06327_gb300 import inputs
+    from paper_1906_06327_gb300.rotgp import Solver
+    stream = torch.cuda.current_stream()
+    precision = w.precision
+    s = Solver(w.n, w.h, gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt,
+               precision=precision, stream=stream.cuda_stream)
+    R = inputs.random_phase_field(w.n[0], w.n[1], w.seed + rank)
+    s.init_analytic(1, R, 1.0, 1.0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def bench_step():
+        s.step_imag(a.inner)
+        return s.observables()
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        bench_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    s.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    obs = None
+    for i in range(a.steps):
+        flush.zero_()  # L2 flush between timed steps, outside the events
+        ev[i][0].record(stream)
+        obs = bench_step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    s.profile(False)
+    kstats = s.profile_read()
+    clk = clocks.stop()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    updates = w.sites * a.inner * a.steps * world
+    value = updates / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    peak, peak_kind = _peaks()
+    dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+    dname, drec = dom
+    avg_ms = drec["total_ms"] / drec["launches"]
+    achieved = drec["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    launches = sum(v["launches"] for v in kstats.values())
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dname),
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": drec["bytes_per_launch"],
+                "avg_launch_ms": avg_ms,
+                "kernel_shares": {k: round(v["total_ms"] / max(1e-9, sum(
+                    x["total_ms"] for x in kstats.values())), 4) for k, v in kstats.items()}}
+
+    e2e = None
+    cpu = None
+    if not a.skip_baselines and rank == 0:
+        # end to end through the public API with pinned host buffers
+        host_in = torch.from_numpy(s.get_psi(fp64=False)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        s.set_psi(host_in)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.e2e_steps):
+            s.set_psi(host_in)
+            s.step_imag(a.inner)
+            s.observables()
+            s.get_psi(host_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_wall = time.perf_counter() - t0
+        e2e_s = max(e2e_wall, e0.elapsed_time(e1) * 1e-3)
+        nbytes = host_in.numel() * host_in.element_size()
+        e2e = {"value": w.sites * a.inner * a.e2e_steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 10 * 8 + 4,
+               "steps": a.e2e_steps, "api": "rotgp_set_psi + rotgp_step_imag + "
+                                            "rotgp_observables + rotgp_get_psi, pinned host"}
+        rate, nsteps, secs = _cpu_oracle_rate(w, a.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nsteps} imaginary-time split step(s) of the {w.name} grid "
+                         f"({secs:.1f} s), FP64 C oracle, 1 thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64+f64" if precision == "fp32" else "c128",
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.n), "spacing": list(w.h),
+                       "physics": {"gamma": w.gamma, "nu": w.nu, "lambda": w.lam, "g": w.g,
+                                   "omega": w.omega, "dt": w.dt},
+                       "split_steps_per_step": a.inner,
+                       "step": f"{a.inner} imaginary-time split steps + observables + "
+                               "vortex count",
+                       "l2": "flushed (512 MiB write) before every timed step; the "
+                             f"{w.sites * (16 if precision == 'fp64' else 8) / 2**20:.0f} MiB "
+                             "state can stay L2-resident within a step",
+                       "parallelism": f"replicas x{world}",
+                       "solver": s.info()},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "wall_s_timed": wall,
+            "final_observables": {k: obs[k] for k in ("norm", "mu", "energy", "vortices")},
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    w = _workload(a.workload)
+    if a.impl == "reference":
+        return run_reference(a, w)
+    return run_ours(a, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * rotgp.h -- C ABI of the GB300 split-step Crank-Nicolson solver for the
+ * rotating Gross-Pitaevskii (GP) equation.
+ *
+ * The method is the one of Kumar, Loncar, Muruganandam, Adhikari and Balaz,
+ * "C and Fortran OpenMP programs for rotating Bose-Einstein condensates",
+ * Sec. 2: the rotating-frame GP equation in dimensionless form (Eq. 3d in 3D,
+ * Eq. 2d in quasi-2D), split into H1 = V + g|psi|^2 (Eq. eq1),
+ * H2 = -(1/2) d^2/dx^2 - i Omega y d/dx (Eq. eq2) and
+ * H3 = -(1/2) d^2/dy^2 + i Omega x d/dy (Eq. eq3) [+ -(1/2) d^2/dz^2 in 3D],
+ * each propagated over the full time step in that order: H1 exactly, the
+ * others by Crank-Nicolson (Eq. eqD.9) with the tridiagonal systems of
+ * Eqs. eqD.11/eq5.  Imaginary time substitutes i Delta -> Delta and
+ * renormalises psi to unit norm after every step.
+ *
+ * Conventions shared by every entry point
+ *  - Grid: n[a] = number of intervals N along axis a (the paper's NX, NY,
+ *    NZ); coordinates x_i = -N_x h_x/2 + i h_x, i = 0..N_x (Sec. 2).  psi is
+ *    zero on every edge (Dirichlet).  Wave functions crossing the ABI hold
+ *    all (N_x+1)(N_y+1)[(N_z+1)] points, edges included, x fastest, as
+ *    interleaved complex numbers (re, im) of float or double.
+ *  - Ownership: the library allocates and owns every device buffer of a
+ *    context.  Caller buffers (src, dst, phase_R, obs) are only read or
+ *    written during the call.  The caller owns the CUDA stream it passes.
+ *  - Asynchrony: step, set and init calls only enqueue work on the context's
+ *    stream.  rotgp_observables, rotgp_get_psi and rotgp_sync synchronise it
+ *    and report errors raised on the device since the last synchronisation
+ *    (a non-finite norm, ROTGP_ENONFINITE).
+ *  - Errors: every int-returning call returns ROTGP_OK (0) or a negative
+ *    code below; rotgp_last_error gives a message.  A context is used by one
+ *    host thread at a time.
+ */
+#ifndef ROTGP_H
+#define ROTGP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ROTGP_OK 0
+#define ROTGP_EINVAL (-1)       /* bad argument                              */
+#define ROTGP_ENOMEM (-2)       /* device or host allocation failed          */
+#define ROTGP_ECUDA (-3)        /* a CUDA runtime call or launch failed      */
+#define ROTGP_ENONFINITE (-4)   /* NaN/Inf norm seen by the step reduction   */
+#define ROTGP_EUNSUPPORTED (-5) /* line systems too weakly diagonally
+                                   dominant for the chunked line solver      */
+
+#define ROTGP_FP64 0 /* complex double throughout                           */
+#define ROTGP_FP32 1 /* complex float bulk; norm, energy, mu, rms in double  */
+
+typedef struct rotgp_ctx rotgp_ctx;
+
+/* dim = 2 or 3; n[a] >= 4 intervals; h[a] > 0.  Entries a >= dim ignored. */
+typedef struct {
+  int dim;
+  int n[3];
+  double h[3];
+} rotgp_grid;
+
+/* Dimensionless physics of Eqs. 3d / 2d: trap anisotropies gamma, nu,
+ * lambda (lambda unused in 2D), nonlinearity g (g_2D in 2D, g_3D in 3D),
+ * rotation frequency omega, time step dt > 0. */
+typedef struct {
+  double gamma, nu, lambda, g, omega, dt;
+} rotgp_phys;
+
+/* Observables of the current state (Sec. 2, Eqs. e2dr/e3dr and e2d/e3d):
+ *  norm      h_x h_y [h_z] sum |psi|^2
+ *  mu, energy      real-part forms (Eqs. e2dr/e3dr, alpha = 1 and 1/2),
+ *                  kinetic term read as -(1/2) psi_R lap psi_R; if
+ *                  sum psi_R^2 < 1e-3 sum |psi|^2 the global phase is first
+ *                  rotated by -i
+ *  mu_c, energy_c  complex forms (Eqs. e2d/e3d)
+ *  rms_*     sqrt(<x^2>), sqrt(<y^2>), sqrt(<z^2>) (0 in 2D), sqrt(<r^2>)
+ *  max_density     max |psi|^2
+ *  step      number of steps taken by this context
+ *  vortices  sum of |winding| over plaquettes of the z = 0 plane inside 0.9
+ *            of the ellipse R^2 = 6<x^2>, 6<y^2> of that plane (not in the
+ *            paper, which counts vortices by eye)
+ *  flags     bit 0: Omega >= min(gamma, nu) (rotating-frame potential not
+ *            confining) */
+typedef struct {
+  double norm, mu, energy, mu_c, energy_c;
+  double rms_x, rms_y, rms_z, rms_r, max_density;
+  long long step;
+  int vortices;
+  int flags;
+} rotgp_obs;
+
+/* Per-kernel timing record (rotgp_profile_read). */
+typedef struct {
+  char name[32];
+  long long launches;
+  double total_ms;
+  double bytes_per_launch; /* algorithmic bytes one launch moves            */
+} rotgp_kstat;
+
+/* Line-solver parameters of a context (rotgp_info). */
+typedef struct {
+  int precision;
+  int halo;        /* H: halo points each chunk re-solves on either side   */
+  int chunk_x;     /* C: output points per chunk, x sweep                  */
+  int chunk_s;     /* C: output points per chunk, y and z sweeps           */
+  int table_len;   /* LU multiplier entries stored per line                */
+  double decay;    /* largest per-point decay factor of a truncated carry  */
+  size_t device_bytes; /* device memory owned by the context               */
+} rotgp_solver_info;
+
+/* Create a context for one condensate on the current CUDA device; stream is
+ * a cudaStream_t (NULL = legacy default stream).  The state is zero until
+ * rotgp_init_analytic or rotgp_set_psi.  Fails with ROTGP_EUNSUPPORTED if
+ * Delta/h^2 is so large that a truncated line carry decays too slowly
+ * (chunk halo above 64 points). */
+int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision,
+                 void* stream, rotgp_ctx** out);
+void rotgp_destroy(rotgp_ctx* ctx);
+
+/* Message of the last error on ctx (or of the last failed rotgp_create on
+ * this thread when ctx is NULL).  Valid until the next call on ctx. */
+const char* rotgp_last_error(const rotgp_ctx* ctx);
+
+/* Change the physics (all fields); rebuilds the per-line tables on the
+ * device.  Same limits as rotgp_create. */
+int rotgp_set_phys(rotgp_ctx* ctx, const rotgp_phys* phys);
+/* Change only Omega (rotation ramps). */
+int rotgp_set_omega(rotgp_ctx* ctx, double omega);
+
+/* Initial state of Eq. fun, normalised to unit norm:
+ *   psi = (x + i y)/sqrt(pi d_xy^2) exp(-(x^2+y^2)/(2 d_xy^2) + 2 pi i R)
+ *   [* (pi d_z^2)^(-1/4) exp(-z^2/(2 d_z^2)) in 3D]
+ * function = 1 (one vortex) or 0 (Gaussian: x + i y -> 1).  phase_R: host
+ * array of (N_x+1)(N_y+1) doubles in [0,1) (x fastest), the random numbers
+ * R(x, y); NULL for no random phase. */
+int rotgp_init_analytic(rotgp_ctx* ctx, int function, const double* phase_R,
+                        double d_xy, double d_z);
+
+/* Load a wave function of (N+1)^d points (see conventions) from host or
+ * device memory, complex double (src_is_fp64 = 1) or complex float.  Values
+ * are taken as they are (not renormalised); edge points are ignored. */
+int rotgp_set_psi(rotgp_ctx* ctx, const void* src, int src_on_device, int src_is_fp64);
+
+/* Store the current wave function into (N+1)^d points of host or device
+ * memory, complex double or float; synchronises the stream. */
+int rotgp_get_psi(rotgp_ctx* ctx, void* dst, int dst_on_device, int dst_is_fp64);
+
+/* Enqueue n split steps in imaginary time (i Delta -> Delta, then
+ * renormalisation) or in real time.  n >= 0. */
+int rotgp_step_imag(rotgp_ctx* ctx, long long n);
+int rotgp_step_real(rotgp_ctx* ctx, long long n);
+
+/* Evaluate the observables of the current state; synchronises the stream. */
+int rotgp_observables(rotgp_ctx* ctx, rotgp_obs* out);
+
+/* Synchronise the stream and report pending device-side errors. */
+int rotgp_sync(rotgp_ctx* ctx);
+
+/* Line-solver parameters chosen for this context. */
+int rotgp_info(const rotgp_ctx* ctx, rotgp_solver_info* out);
+
+/* Per-kernel CUDA-event timing.  While enabled, every kernel launch of the
+ * context is bracketed by events on its stream.  rotgp_profile_read
+ * synchronises, fills up to max records (one per kernel name), sets *count
+ * and clears the accumulated records. */
+int rotgp_profile_enable(rotgp_ctx* ctx, int on);
+int rotgp_profile_read(rotgp_ctx* ctx, rotgp_kstat* out, int max, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROTGP_H */

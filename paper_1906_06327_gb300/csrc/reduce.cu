@@ -1,0 +1,292 @@
+// reduce.cu -- the read-only reductions over a state: the observables of
+// Sec. 2 (norm, real-part mu and E of Eqs. e2dr/e3dr, complex forms of
+// Eqs. e2d/e3d, rms sizes), the vortex count diagnostic, and the plain norm
+// used after loading a state.
+//
+// Every reduction is one pass over the state: each thread accumulates its
+// sites in registers, blocks reduce with warp shuffles and write one partial
+// per block, and the last block to finish (atomic ticket) combines the
+// partials in block order, so results are deterministic run to run.  The
+// pending imaginary-time scale is applied as the state is read.
+#include "common.cuh"
+
+namespace rotgp {
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Reduce q[0..NV) over the block (entry NV-1 with max if MAXLAST), store the
+// block partial, and return true in the block that finishes last (whose
+// threads must then combine the partials).
+template <int NV, bool MAXLAST>
+__device__ bool block_partials(double* q, double* partials, unsigned* counter) {
+  __shared__ double ws[32][NV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double x = (MAXLAST && v == NV - 1) ? wmax(q[v]) : wsum(q[v]);
+    if (lane == 0) ws[warp][v] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int v = threadIdx.x;
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s = (MAXLAST && v == NV - 1) ? fmax(s, ws[w][v]) : s + ws[w][v];
+    partials[(size_t)blockIdx.x * NV + v] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// In the last block: thread v < NV sums partial v over all blocks in order.
+template <int NV, bool MAXLAST>
+__device__ double combine(const double* partials, int v) {
+  double s = 0;
+  for (unsigned b = 0; b < gridDim.x; ++b) {
+    const double x = __ldcg(&partials[(size_t)b * NV + v]);
+    s = (MAXLAST && v == NV - 1) ? fmax(s, x) : s + x;
+  }
+  return s;
+}
+
+// ------------------------------------------------------------ observables
+// Per interior site (edges are zero and contribute nothing), with the
+// 3-point Laplacian lap and central differences D of the CN sweeps:
+//   q0 |psi|^2   q1 psi_R^2   q2 psi_I^2
+//   q3 psi_R (-lap psi_R/2 + V psi_R + Omega (y D_x psi_I - x D_y psi_I))
+//   q4 g |psi|^2 psi_R^2
+//   q5, q6  the same two for the state rotated by -i (R <- I, I <- -R)
+//   q7 Re psi^* (-lap/2 + V - Omega L_z) psi, L_z = i (y D_x - x D_y)
+//   q8 g |psi|^4   q9..q11  x^2, y^2, z^2 times |psi|^2   q12 max |psi|^2
+template <class T>
+__global__ void __launch_bounds__(256) k_observables(const obs_args a) {
+  using C = cpx<T>;
+  const C* psi = static_cast<const C*>(a.psi);
+  const long long nx = a.nx, ny = a.ny, nz = a.nz;
+  const long long sites = nx * ny * nz;
+  const T s = (T)(*a.scale);
+  const T ihx2 = (T)(1.0 / (a.hx * a.hx)), ihy2 = (T)(1.0 / (a.hy * a.hy));
+  const T ihz2 = a.dim == 3 ? (T)(1.0 / (a.hz * a.hz)) : (T)0;
+  const T i2hx = (T)(0.5 / a.hx), i2hy = (T)(0.5 / a.hy);
+  const T om = (T)a.omega, g = (T)a.g;
+  double q[NQ];
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) q[v] = 0.0;
+  auto at = [&](long long i, long long j, long long k) -> C {
+    if (i >= nx || j >= ny || k >= nz) return mk<T>(0, 0);  // implicit edge N
+    return s * psi[(k * ny + j) * nx + i];
+  };
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < sites;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx % nx, j = (idx / nx) % ny, k = idx / (nx * ny);
+    if (i == 0 || j == 0 || (a.dim == 3 && k == 0)) continue;
+    const T x = (T)(a.x0 + (double)i * a.hx), y = (T)(a.y0 + (double)j * a.hy);
+    const T z = a.dim == 3 ? (T)(a.z0 + (double)k * a.hz) : (T)0;
+    const T V = (T)a.hgam2 * x * x + (T)a.hnu2 * y * y + (T)a.hlam2 * z * z;
+    const C c = s * psi[idx];
+    const C xp = at(i + 1, j, k), xm = at(i - 1, j, k);
+    const C yp = at(i, j + 1, k), ym = at(i, j - 1, k);
+    C lap = ihx2 * (xp + xm - (T)2 * c) + ihy2 * (yp + ym - (T)2 * c);
+    if (a.dim == 3) lap = lap + ihz2 * (at(i, j, k + 1) + at(i, j, k - 1) - (T)2 * c);
+    const C dx = i2hx * (xp - xm), dy = i2hy * (yp - ym);
+    const T re = c.x, im = c.y, dens = re * re + im * im;
+    const T hr = (T)-0.5 * lap.x + V * re + om * (y * dx.y - x * dy.y);
+    const T hi = (T)-0.5 * lap.y + V * im + om * (-(y * dx.x) + x * dy.x);
+    // -Omega L_z psi = -Omega i (y D_x - x D_y) psi
+    const C lz = y * dx - x * dy;  // L_z psi / i
+    const C hlin = mk<T>((T)-0.5 * lap.x + V * c.x + om * lz.y,
+                         (T)-0.5 * lap.y + V * c.y - om * lz.x);
+    q[0] += (double)dens;
+    q[1] += (double)(re * re);
+    q[2] += (double)(im * im);
+    q[3] += (double)(re * hr);
+    q[4] += (double)(g * dens * re * re);
+    q[5] += (double)(im * hi);
+    q[6] += (double)(g * dens * im * im);
+    q[7] += (double)(re * hlin.x + im * hlin.y);
+    q[8] += (double)(g * dens * dens);
+    q[9] += (double)(x * x * dens);
+    q[10] += (double)(y * y * dens);
+    q[11] += (double)(z * z * dens);
+    q[12] = fmax(q[12], (double)dens);
+  }
+  if (!block_partials<NQ, true>(q, a.partials, a.counter)) return;
+  __shared__ double fin[NQ];
+  __threadfence();
+  if (threadIdx.x < NQ) fin[threadIdx.x] = combine<NQ, true>(a.partials, threadIdx.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double vol = a.hx * a.hy * (a.dim == 3 ? a.hz : 1.0);
+    const bool rot = fin[1] < 1e-3 * fin[0];
+    const double lin = rot ? fin[5] : fin[3], nl = rot ? fin[6] : fin[4];
+    const double den = rot ? fin[2] : fin[1];
+    double* r = a.result;
+    r[0] = vol * fin[0];
+    r[1] = (lin + nl) / den;
+    r[2] = (lin + 0.5 * nl) / den;
+    r[3] = (fin[7] + fin[8]) / fin[0];
+    r[4] = (fin[7] + 0.5 * fin[8]) / fin[0];
+    r[5] = sqrt(fin[9] / fin[0]);
+    r[6] = sqrt(fin[10] / fin[0]);
+    r[7] = a.dim == 3 ? sqrt(fin[11] / fin[0]) : 0.0;
+    r[8] = sqrt((fin[9] + fin[10] + fin[11]) / fin[0]);
+    r[9] = fin[12];
+    *a.counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------ vortex count
+// Pass 1: density moments of the plane k = kplane (double): sum rho,
+// sum x^2 rho, sum y^2 rho -> R_x^2 = 6 <x^2>, R_y^2 = 6 <y^2>.
+template <class T>
+__global__ void __launch_bounds__(256) k_vort_moments(const vort_args a) {
+  using C = cpx<T>;
+  const C* pl = static_cast<const C*>(a.psi) + (size_t)a.kplane * a.nx * a.ny;
+  const long long n = (long long)a.nx * a.ny;
+  double q[3] = {0, 0, 0};
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % a.nx), j = (int)(idx / a.nx);
+    const C c = pl[idx];
+    const double d = (double)c.x * c.x + (double)c.y * c.y;
+    const double x = a.x0 + i * a.hx, y = a.y0 + j * a.hy;
+    q[0] += d;
+    q[1] += x * x * d;
+    q[2] += y * y * d;
+  }
+  if (!block_partials<3, false>(q, a.partials, a.counter)) return;
+  __shared__ double fin[3];
+  __threadfence();
+  if (threadIdx.x < 3) fin[threadIdx.x] = combine<3, false>(a.partials, threadIdx.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.moments[0] = fin[0] > 0 ? 6.0 * fin[1] / fin[0] : 0.0;
+    a.moments[1] = fin[0] > 0 ? 6.0 * fin[2] / fin[0] : 0.0;
+    *a.count = 0;
+    *a.counter = 0u;
+  }
+}
+
+__device__ __forceinline__ float atan2_t(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double atan2_t(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ int round_half_away(float v) { return (int)roundf(v); }
+__device__ __forceinline__ int round_half_away(double v) { return (int)round(v); }
+
+// Pass 2: one thread per plaquette (i,j)..(i+1,j+1) touching no edge and
+// centred inside 0.9 of the ellipse: winding = round(sum of
+// arg(psi_b conj(psi_a)) around the loop / 2 pi), computed in T.
+template <class T>
+__global__ void __launch_bounds__(256) k_vort_count(const vort_args a) {
+  using C = cpx<T>;
+  const C* pl = static_cast<const C*>(a.psi) + (size_t)a.kplane * a.nx * a.ny;
+  const double rx2 = a.moments[0], ry2 = a.moments[1];
+  const long long n = (long long)a.nx * a.ny;
+  int cnt = 0;
+  if (rx2 > 0 && ry2 > 0) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+      const int i = (int)(idx % a.nx), j = (int)(idx / a.nx);
+      // corners i..i+1 must avoid both edges 0 and N (N = nx implicit)
+      if (i < 1 || j < 1 || i + 1 > a.nx - 1 || j + 1 > a.ny - 1) continue;
+      const double xc = a.x0 + i * a.hx + 0.5 * a.hx, yc = a.y0 + j * a.hy + 0.5 * a.hy;
+      if (!(xc * xc / rx2 + yc * yc / ry2 < 0.81)) continue;
+      C q[4] = {pl[idx], pl[idx + 1], pl[idx + 1 + a.nx], pl[idx + a.nx]};
+      T w = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const C u = q[(t + 1) & 3], v = q[t];
+        const T pr = u.x * v.x + u.y * v.y;
+        const T pim = u.y * v.x - u.x * v.y;
+        w += atan2_t(pim, pr);
+      }
+      const int wn = round_half_away(w / (T)6.28318530717958647692);
+      cnt += wn < 0 ? -wn : wn;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.count, cnt);
+}
+
+// ------------------------------------------------------------ plain norm
+template <class T>
+__global__ void __launch_bounds__(256) k_norm(const void* psi_v, long long n, double vol,
+                                              int imag_scale, double* partials,
+                                              unsigned* counter, double* scale_out,
+                                              double* norm_out, int* flags) {
+  const cpx<T>* psi = static_cast<const cpx<T>*>(psi_v);
+  double q[1] = {0.0};
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x)
+    q[0] += (double)abs2(psi[idx]);
+  if (!block_partials<1, false>(q, partials, counter)) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    const double nrm = combine<1, false>(partials, 0) * vol;
+    *norm_out = nrm;
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+      atomicOr(flags, 1);
+      *scale_out = 1.0;
+    } else {
+      *scale_out = imag_scale ? 1.0 / sqrt(nrm) : 1.0;
+    }
+    *counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_observables(bool fp64, const obs_args& a, int blocks, int threads,
+                               cudaStream_t s) {
+  if (fp64)
+    k_observables<double><<<blocks, threads, 0, s>>>(a);
+  else
+    k_observables<float><<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vortex_moments(bool fp64, const vort_args& a, int blocks, int threads,
+                                  cudaStream_t s) {
+  if (fp64)
+    k_vort_moments<double><<<blocks, threads, 0, s>>>(a);
+  else
+    k_vort_moments<float><<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vortex_count(bool fp64, const vort_args& a, int blocks, int threads,
+                                cudaStream_t s) {
+  if (fp64)
+    k_vort_count<double><<<blocks, threads, 0, s>>>(a);
+  else
+    k_vort_count<float><<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm(bool fp64, const void* psi, long long nsites, double vol, int imag_scale,
+                        double* partials, unsigned int* counter, double* scale_out,
+                        double* norm_out, int* flags, int blocks, int threads, cudaStream_t s) {
+  if (fp64)
+    k_norm<double><<<blocks, threads, 0, s>>>(psi, nsites, vol, imag_scale, partials, counter,
+                                              scale_out, norm_out, flags);
+  else
+    k_norm<float><<<blocks, threads, 0, s>>>(psi, nsites, vol, imag_scale, partials, counter,
+                                             scale_out, norm_out, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace rotgp

@@ -1,0 +1,773 @@
+// rotgp.cu -- host side of the C ABI declared in include/rotgp.h: context
+// lifetime, solver sizing, launch plans of one split step (Sec. 2: H1 fused
+// into the x sweep, then the y sweep and, in 3D, the z sweep, with the norm
+// reduced in the last sweep), observables, state I/O and kernel timing.
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rotgp.h"
+#include "common.cuh"
+
+using namespace rotgp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kMaxHalo = 64;
+constexpr int kMaxTable = 512;
+
+enum KernelId {
+  K_SWEEP_X, K_SWEEP_Y, K_SWEEP_Z, K_OBS, K_VMOM, K_VCOUNT, K_NORM, K_INIT, K_IO, K_TABLES,
+  K_COUNT
+};
+const char* kKernelNames[K_COUNT] = {"sweep_x_h1", "sweep_y",        "sweep_z",
+                                     "observables", "vortex_moments", "vortex_count",
+                                     "norm",        "init_analytic",  "pack_unpack",
+                                     "tables"};
+
+struct AxisPlan {
+  int nlines = 0;       // lines with distinct coefficients (table rows)
+  axis_coef co[2];      // [mode] 0 = real, 1 = imaginary
+  void* table[2] = {nullptr, nullptr};
+};
+
+struct ProfRec {
+  int kid;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct rotgp_ctx {
+  rotgp_grid grid{};
+  rotgp_phys phys{};
+  int prec = ROTGP_FP32;
+  bool fp64 = false;
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, nz = 1;  // stored points
+  long long sites = 0;
+  size_t elem = 8;
+  double x0 = 0, y0 = 0, z0 = 0, vol = 1;
+  // solver sizing
+  int halo = 2, chunk_x = 32, chunk_s = 32, lt = 8;
+  double decay = 0;
+  int warps_x = 4, pitch_x = 0, cpb_s = 4;
+  // device memory
+  void* psi[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  double* dR = nullptr;
+  AxisPlan axis[3];
+  double* partials = nullptr;
+  size_t partial_doubles = 0;
+  unsigned* counter = nullptr;
+  double* scalars = nullptr;  // [0] scale, [1] norm, [2..2+NOBS) obs, [+2] moments
+  int* iflags = nullptr;      // [0] flags, [1] vortex count
+  double* h_obs = nullptr;    // pinned: NOBS doubles + 2 ints
+  size_t device_bytes = 0;
+  long long steps = 0;
+  std::string err;
+  // profiling
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  double bytes_per_launch[K_COUNT] = {0};
+  int sm_count = 148;
+  int smem_optin = 232448;
+
+  double* d_scale() { return scalars; }
+  double* d_norm() { return scalars + 1; }
+  double* d_obs() { return scalars + 2; }
+  double* d_moments() { return scalars + 2 + NOBS; }
+  int* d_flags() { return iflags; }
+  int* d_count() { return iflags + 1; }
+};
+
+namespace {
+
+int fail(rotgp_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(rotgp_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, ROTGP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+using cd = std::complex<double>;
+
+// Coefficients of Eqs. eqD.11/eq5 for one axis and mode (see axis_coef):
+// kappa = (i Delta | Delta)/(4 h^2); tau_unit multiplies the line's
+// coordinate: x lines (u = y_j): real -Delta Omega/(4h), imaginary
+// +i Delta Omega/(4h); y lines (u = x_i): the negatives (Omega y -> -Omega x);
+// z lines: 0.
+axis_coef make_coef(int axis, int imag, double h, double dt, double omega, double u0, double du) {
+  axis_coef co{};
+  const cd idt = imag ? cd(dt, 0) : cd(0, dt);
+  const cd kap = idt / (4.0 * h * h);
+  cd tau_unit(0, 0);
+  const cd dplain = idt / cd(0, 1);  // Delta in real time, -i Delta in imaginary time
+  if (axis == 0) tau_unit = -dplain * omega / (4.0 * h);
+  if (axis == 1) tau_unit = dplain * omega / (4.0 * h);
+  co.kap_re = kap.real();
+  co.kap_im = kap.imag();
+  co.tau_re = tau_unit.real();
+  co.tau_im = tau_unit.imag();
+  co.u0 = u0;
+  co.du = du;
+  return co;
+}
+
+// Worst-case carry decay and multiplier-table length over the lines of an
+// axis: iterate c'_p = A+ / (A0 - A- c'_{p-1}) to its fixed point c*, then
+// forward decay |A- m*|, backward decay |c*|.
+void size_axis(const axis_coef& co, int nlines, double* decay, int* lt) {
+  for (int l = 0; l < nlines; ++l) {
+    const double u = co.u0 + l * co.du;
+    const cd kap(co.kap_re, co.kap_im), tau = cd(co.tau_re, co.tau_im) * u;
+    const cd a0 = 1.0 + 2.0 * kap, am = -kap + tau, ap = -kap - tau;
+    cd c(0, 0), m(0, 0);
+    int p = 1;
+    for (; p <= kMaxTable; ++p) {
+      m = 1.0 / (a0 - am * c);
+      const cd cn = ap * m;
+      const bool conv = std::abs(cn - c) <= 1e-17 * std::abs(cn);
+      c = cn;
+      if (conv) break;
+    }
+    *lt = std::max(*lt, std::min(p + 1, kMaxTable));
+    *decay = std::max(*decay, std::max(std::abs(am * m), std::abs(c)));
+  }
+}
+
+double nlines_u0(const rotgp_ctx* c, int axis) {
+  return axis == 0 ? c->y0 : (axis == 1 ? c->x0 : 0.0);
+}
+double nlines_du(const rotgp_ctx* c, int axis) {
+  return axis == 0 ? c->grid.h[1] : (axis == 1 ? c->grid.h[0] : 0.0);
+}
+
+// Size the line solver for the current physics (both modes).
+int plan_solver(rotgp_ctx* c, int* halo, int* lt, double* decay) {
+  double dec = 0;
+  int tl = 2;
+  for (int a = 0; a < c->grid.dim; ++a) {
+    const int nl = a == 0 ? c->ny : (a == 1 ? c->nx : 1);
+    for (int mode = 0; mode < 2; ++mode) {
+      axis_coef co = make_coef(a, mode, c->grid.h[a], c->phys.dt, c->phys.omega,
+                               nlines_u0(c, a), nlines_du(c, a));
+      size_axis(co, nl, &dec, &tl);
+    }
+  }
+  if (!(dec < 1.0) || !std::isfinite(dec))
+    return fail(c, ROTGP_EUNSUPPORTED, "line carry does not decay (factor %g)", dec);
+  const double tol = c->fp64 ? 1e-17 : 1e-9;
+  int H = dec <= 0 ? 1 : (int)std::ceil(std::log(tol) / std::log(dec)) + 1;
+  H = std::max(H, 2);
+  if (H > kMaxHalo)
+    return fail(c, ROTGP_EUNSUPPORTED,
+                "chunk halo %d > %d: Delta/h^2 too large for the chunked line solver "
+                "(carry decay factor %.3f)",
+                H, kMaxHalo, dec);
+  *halo = H;
+  *lt = tl;
+  *decay = dec;
+  return ROTGP_OK;
+}
+
+int choose_layout(rotgp_ctx* c) {
+  const int H = c->halo;
+  const int C = H <= 8 ? 32 : 64;
+  c->chunk_x = C;
+  c->chunk_s = C;
+  const int W = C + 2 * H + 2;
+  c->pitch_x = (W % 2) ? W : W + 1;
+  const size_t limit = (size_t)c->smem_optin - 1024;  // static shared memory reserve
+  const size_t per_warp = (size_t)32 * c->pitch_x * c->elem;
+  c->warps_x = 4;
+  while (c->warps_x > 1 && per_warp * c->warps_x > limit) c->warps_x /= 2;
+  if (per_warp > limit) return fail(c, ROTGP_EUNSUPPORTED, "x tile too large");
+  const size_t per_s = (size_t)32 * W * c->elem;
+  c->cpb_s = 4;
+  while (c->cpb_s > 1 && per_s * c->cpb_s > limit) c->cpb_s /= 2;
+  if (per_s > limit) return fail(c, ROTGP_EUNSUPPORTED, "strided tile too large");
+  return ROTGP_OK;
+}
+
+long long strided_blocks(const rotgp_ctx* c, int axis) {
+  const long long ncols = axis == 1 ? (long long)c->nx * c->nz : (long long)c->nx * c->ny;
+  const int len = axis == 1 ? c->ny : c->nz;
+  const int nch = (len + c->chunk_s - 1) / c->chunk_s;
+  return ((ncols + 31) / 32) * ((nch + c->cpb_s - 1) / c->cpb_s);
+}
+
+int reduce_blocks(const rotgp_ctx* c, long long n) {
+  long long b = (n + 255) / 256;
+  const long long cap = (long long)c->sm_count * 8;
+  return (int)std::max(1LL, std::min(b, cap));
+}
+
+// --------------------------------------------------------------- profiling
+cudaEvent_t take_event(rotgp_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Timed {
+  rotgp_ctx* c;
+  int kid;
+  cudaEvent_t a = nullptr;
+  Timed(rotgp_ctx* cc, int k) : c(cc), kid(k) {
+    if (c->prof) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Timed() {
+    if (c->prof) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->recs.push_back({kid, a, b});
+    }
+  }
+};
+
+int build_tables(rotgp_ctx* c) {
+  for (int a = 0; a < c->grid.dim; ++a) {
+    AxisPlan& ap = c->axis[a];
+    for (int mode = 0; mode < 2; ++mode) {
+      ap.co[mode] = make_coef(a, mode, c->grid.h[a], c->phys.dt, c->phys.omega,
+                              nlines_u0(c, a), nlines_du(c, a));
+      Timed t(c, K_TABLES);
+      cudaError_t e = launch_tables(c->fp64, ap.table[mode], ap.nlines, c->lt, ap.co[mode],
+                                    c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "table kernel");
+    }
+  }
+  return ROTGP_OK;
+}
+
+// --------------------------------------------------------------- one step
+int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
+  const int mode = imag ? 1 : 0;
+  sweep_args a{};
+  a.in = c->psi[c->cur];
+  a.out = c->psi[1 - c->cur];
+  a.table = c->axis[axis].table[mode];
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.halo = c->halo;
+  a.lt = c->lt;
+  a.co = c->axis[axis].co[mode];
+  a.vol = c->vol;
+  a.imag = imag ? 1 : 0;
+  a.partials = c->partials;
+  a.counter = c->counter;
+  a.scale_out = c->d_scale();
+  a.norm_out = c->d_norm();
+  a.flags = c->d_flags();
+  cudaError_t e;
+  if (axis == 0) {
+    a.len = c->nx;
+    a.stride = 1;
+    a.chunk = c->chunk_x;
+    a.nchunks = (c->nx + c->chunk_x - 1) / c->chunk_x;
+    a.pitch = c->pitch_x;
+    a.h1 = 1;
+    a.dt = c->phys.dt;
+    a.g = c->phys.g;
+    a.hgam2 = 0.5 * c->phys.gamma * c->phys.gamma;
+    a.hnu2 = 0.5 * c->phys.nu * c->phys.nu;
+    a.hlam2 = c->grid.dim == 3 ? 0.5 * c->phys.lambda * c->phys.lambda : 0.0;
+    a.x0 = c->x0;
+    a.hx = c->grid.h[0];
+    a.y0 = c->y0;
+    a.hy = c->grid.h[1];
+    a.z0 = c->z0;
+    a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
+    a.scale = c->d_scale();
+    const long long rows = (long long)c->ny * c->nz;
+    const long long tiles = ((rows + 31) / 32) * a.nchunks;
+    const int blocks = (int)((tiles + c->warps_x - 1) / c->warps_x);
+    const size_t smem = (size_t)c->warps_x * 32 * c->pitch_x * c->elem;
+    Timed t(c, K_SWEEP_X);
+    e = launch_sweep_x(c->fp64, imag, a, blocks, 32 * c->warps_x, smem, c->stream);
+  } else {
+    a.len = axis == 1 ? c->ny : c->nz;
+    a.stride = axis == 1 ? (long long)c->nx : (long long)c->nx * c->ny;
+    a.ncols = axis == 1 ? (long long)c->nx * c->nz : (long long)c->nx * c->ny;
+    a.outer = axis == 1 ? (long long)c->nx * c->ny : (long long)c->nx;
+    a.tab_mod = axis == 1 ? 1 : 0;
+    a.chunk = c->chunk_s;
+    a.nchunks = (a.len + c->chunk_s - 1) / c->chunk_s;
+    a.reduce = last ? 1 : 0;
+    const int W = c->chunk_s + 2 * c->halo + 2;
+    const size_t smem = (size_t)c->cpb_s * 32 * W * c->elem;
+    const int gx = (int)((a.ncols + 31) / 32);
+    Timed t(c, axis == 1 ? K_SWEEP_Y : K_SWEEP_Z);
+    e = launch_sweep_strided(c->fp64, a, gx, 32, c->cpb_s, smem, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+  c->cur = 1 - c->cur;
+  return ROTGP_OK;
+}
+
+int run_steps(rotgp_ctx* c, long long n, bool imag) {
+  if (!c) return ROTGP_EINVAL;
+  if (n < 0) return fail(c, ROTGP_EINVAL, "negative step count");
+  for (long long s = 0; s < n; ++s) {
+    for (int a = 0; a < c->grid.dim; ++a) {
+      int rc = sweep(c, a, imag, a == c->grid.dim - 1);
+      if (rc) return rc;
+    }
+    ++c->steps;
+  }
+  return ROTGP_OK;
+}
+
+int check_flags(rotgp_ctx* c) {
+  int flags = 0;
+  cudaError_t e = cudaMemcpyAsync(&flags, c->d_flags(), sizeof(int), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+  if (flags & 1) return fail(c, ROTGP_ENONFINITE, "non-finite or zero norm in a reduction");
+  return ROTGP_OK;
+}
+
+bool finite_phys(const rotgp_phys* p) {
+  const double v[6] = {p->gamma, p->nu, p->lambda, p->g, p->omega, p->dt};
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return p->dt > 0;
+}
+
+void release(rotgp_ctx* c) {
+  for (void*& p : c->psi) cudaFree(p), p = nullptr;
+  cudaFree(c->staging);
+  cudaFree(c->dR);
+  for (auto& ap : c->axis)
+    for (void*& t : ap.table) cudaFree(t), t = nullptr;
+  cudaFree(c->partials);
+  cudaFree(c->counter);
+  cudaFree(c->scalars);
+  cudaFree(c->iflags);
+  if (c->h_obs) cudaFreeHost(c->h_obs);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+}
+
+int dev_alloc(rotgp_ctx* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, ROTGP_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  c->device_bytes += bytes;
+  return ROTGP_OK;
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+const char* rotgp_last_error(const rotgp_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, void* stream,
+                 rotgp_ctx** out) {
+  g_create_error.clear();
+  if (!grid || !phys || !out) return fail(nullptr, ROTGP_EINVAL, "null argument");
+  *out = nullptr;
+  if (grid->dim != 2 && grid->dim != 3) return fail(nullptr, ROTGP_EINVAL, "dim must be 2 or 3");
+  for (int a = 0; a < grid->dim; ++a) {
+    if (grid->n[a] < 4) return fail(nullptr, ROTGP_EINVAL, "n[%d] = %d < 4", a, grid->n[a]);
+    if (!(grid->h[a] > 0) || !std::isfinite(grid->h[a]))
+      return fail(nullptr, ROTGP_EINVAL, "h[%d] must be positive", a);
+  }
+  if (precision != ROTGP_FP32 && precision != ROTGP_FP64)
+    return fail(nullptr, ROTGP_EINVAL, "precision must be ROTGP_FP32 or ROTGP_FP64");
+  if (!finite_phys(phys)) return fail(nullptr, ROTGP_EINVAL, "physics must be finite, dt > 0");
+  const long long pts = (long long)grid->n[0] * grid->n[1] * (grid->dim == 3 ? grid->n[2] : 1);
+  if (pts > (1LL << 34)) return fail(nullptr, ROTGP_EINVAL, "grid too large");
+
+  rotgp_ctx* c = new (std::nothrow) rotgp_ctx();
+  if (!c) return fail(nullptr, ROTGP_ENOMEM, "host allocation failed");
+  c->grid = *grid;
+  c->phys = *phys;
+  c->prec = precision;
+  c->fp64 = precision == ROTGP_FP64;
+  c->elem = c->fp64 ? 16 : 8;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->nx = grid->n[0];
+  c->ny = grid->n[1];
+  c->nz = grid->dim == 3 ? grid->n[2] : 1;
+  c->sites = pts;
+  c->x0 = -0.5 * grid->n[0] * grid->h[0];
+  c->y0 = -0.5 * grid->n[1] * grid->h[1];
+  c->z0 = grid->dim == 3 ? -0.5 * grid->n[2] * grid->h[2] : 0.0;
+  c->vol = grid->h[0] * grid->h[1] * (grid->dim == 3 ? grid->h[2] : 1.0);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    int rc = fail(nullptr, ROTGP_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    delete c;
+    return rc;
+  }
+  int rc = plan_solver(c, &c->halo, &c->lt, &c->decay);
+  if (!rc) rc = choose_layout(c);
+  if (rc) {
+    g_create_error = c->err;
+    delete c;
+    return rc;
+  }
+  c->axis[0].nlines = c->ny;
+  c->axis[1].nlines = c->nx;
+  c->axis[2].nlines = 1;
+  // reduction scratch: the largest per-block partial count of any reduction
+  size_t pd = (size_t)reduce_blocks(c, c->sites) * NQ;
+  for (int a = 1; a < grid->dim; ++a) pd = std::max(pd, (size_t)strided_blocks(c, a));
+  pd = std::max(pd, (size_t)reduce_blocks(c, (long long)c->nx * c->ny) * 3);
+  c->partial_doubles = pd;
+  c->staging_bytes = (size_t)(grid->n[0] + 1) * (grid->n[1] + 1) *
+                     (grid->dim == 3 ? grid->n[2] + 1 : 1) * 16;
+  const size_t state = (size_t)c->sites * c->elem;
+  const size_t tab_elem = c->fp64 ? sizeof(lu_entry<double>) : sizeof(lu_entry<float>);
+  rc = dev_alloc(c, &c->psi[0], state);
+  if (!rc) rc = dev_alloc(c, &c->psi[1], state);
+  if (!rc) rc = dev_alloc(c, &c->staging, c->staging_bytes);
+  if (!rc) rc = dev_alloc(c, (void**)&c->dR, (size_t)(grid->n[0] + 1) * (grid->n[1] + 1) * 8);
+  for (int a = 0; a < grid->dim && !rc; ++a)
+    for (int m = 0; m < 2 && !rc; ++m)
+      rc = dev_alloc(c, &c->axis[a].table[m], (size_t)c->axis[a].nlines * (c->lt + 1) * tab_elem);
+  if (!rc) rc = dev_alloc(c, (void**)&c->partials, c->partial_doubles * sizeof(double));
+  if (!rc) rc = dev_alloc(c, (void**)&c->counter, sizeof(unsigned));
+  if (!rc) rc = dev_alloc(c, (void**)&c->scalars, (2 + NOBS + 2) * sizeof(double));
+  if (!rc) rc = dev_alloc(c, (void**)&c->iflags, 2 * sizeof(int));
+  if (!rc && cudaMallocHost((void**)&c->h_obs, (NOBS + 2) * sizeof(double)) != cudaSuccess)
+    rc = fail(c, ROTGP_ENOMEM, "pinned host allocation failed");
+  if (!rc) {
+    e = cudaMemsetAsync(c->psi[0], 0, state, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->psi[1], 0, state, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->iflags, 0, 2 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_set_scalar(c->d_scale(), 1.0, c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "initialise buffers");
+  }
+  if (!rc) rc = build_tables(c);
+  if (!rc) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(c, e, "create");
+  }
+  if (rc) {
+    g_create_error = c->err;
+    release(c);
+    delete c;
+    return rc;
+  }
+  // algorithmic bytes per launch: one read + one write of the state per sweep
+  c->bytes_per_launch[K_SWEEP_X] = 2.0 * state;
+  c->bytes_per_launch[K_SWEEP_Y] = 2.0 * state;
+  c->bytes_per_launch[K_SWEEP_Z] = 2.0 * state;
+  c->bytes_per_launch[K_OBS] = 1.0 * state;
+  *out = c;
+  return ROTGP_OK;
+}
+
+void rotgp_destroy(rotgp_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  release(ctx);
+  delete ctx;
+}
+
+int rotgp_set_phys(rotgp_ctx* c, const rotgp_phys* phys) {
+  if (!c || !phys) return ROTGP_EINVAL;
+  if (!finite_phys(phys)) return fail(c, ROTGP_EINVAL, "physics must be finite, dt > 0");
+  const rotgp_phys old = c->phys;
+  c->phys = *phys;
+  int halo = 0, lt = 0;
+  double dec = 0;
+  int rc = plan_solver(c, &halo, &lt, &dec);
+  if (!rc && lt > c->lt) {
+    // tables were sized at create; a longer table needs more memory
+    rc = fail(c, ROTGP_EUNSUPPORTED, "new physics needs %d table entries (context has %d)", lt,
+              c->lt);
+  }
+  if (!rc && halo > c->halo) {
+    const int old_h = c->halo;
+    c->halo = halo;
+    rc = choose_layout(c);
+    if (!rc) {
+      // partial buffer size depends on the strided launch shape
+      for (int a = 1; a < c->grid.dim; ++a)
+        if ((size_t)strided_blocks(c, a) > c->partial_doubles)
+          rc = fail(c, ROTGP_EUNSUPPORTED, "new physics needs a larger reduction buffer");
+    }
+    if (rc) {
+      c->halo = old_h;
+      choose_layout(c);
+    }
+  }
+  if (rc) {
+    c->phys = old;
+    return rc;
+  }
+  c->decay = std::max(c->decay, dec);
+  return build_tables(c);
+}
+
+int rotgp_set_omega(rotgp_ctx* c, double omega) {
+  if (!c) return ROTGP_EINVAL;
+  rotgp_phys p = c->phys;
+  p.omega = omega;
+  return rotgp_set_phys(c, &p);
+}
+
+int rotgp_init_analytic(rotgp_ctx* c, int function, const double* phase_R, double d_xy,
+                        double d_z) {
+  if (!c) return ROTGP_EINVAL;
+  if (function != 0 && function != 1) return fail(c, ROTGP_EINVAL, "function must be 0 or 1");
+  if (!(d_xy > 0) || (c->grid.dim == 3 && !(d_z > 0)))
+    return fail(c, ROTGP_EINVAL, "widths must be positive");
+  cudaError_t e = cudaSuccess;
+  if (phase_R) {
+    e = cudaMemcpyAsync(c->dR, phase_R, (size_t)(c->nx + 1) * (c->ny + 1) * 8,
+                        cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy phase field");
+  }
+  {
+    Timed t(c, K_INIT);
+    e = launch_init_analytic(c->fp64, c->psi[c->cur], c->nx, c->ny, c->nz, c->grid.dim, c->x0,
+                             c->grid.h[0], c->y0, c->grid.h[1], c->z0,
+                             c->grid.dim == 3 ? c->grid.h[2] : 0.0, function,
+                             phase_R ? c->dR : nullptr, d_xy, d_z, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  if ((e = cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "reset flags");
+  {
+    Timed t(c, K_NORM);
+    e = launch_norm(c->fp64, c->psi[c->cur], c->sites, c->vol, 1, c->partials, c->counter,
+                    c->d_scale(), c->d_norm(), c->d_flags(), reduce_blocks(c, c->sites), 256,
+                    c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "norm kernel");
+  c->steps = 0;
+  return check_flags(c);  // also releases phase_R
+}
+
+int rotgp_set_psi(rotgp_ctx* c, const void* src, int src_on_device, int src_is_fp64) {
+  if (!c || !src) return c ? fail(c, ROTGP_EINVAL, "null source") : ROTGP_EINVAL;
+  const size_t pts = c->staging_bytes / 16;
+  const size_t bytes = pts * (src_is_fp64 ? 16 : 8);
+  const void* from = src;
+  cudaError_t e = cudaSuccess;
+  if (!src_on_device) {
+    e = cudaMemcpyAsync(c->staging, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy state to device");
+    from = c->staging;
+  }
+  {
+    Timed t(c, K_IO);
+    e = launch_pack(c->fp64, src_is_fp64 != 0, from, c->psi[c->cur], c->nx, c->ny, c->nz,
+                    c->grid.dim, c->d_scale(), c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
+  if ((e = cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "reset flags");
+  c->steps = 0;
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_psi");
+  return ROTGP_OK;
+}
+
+int rotgp_get_psi(rotgp_ctx* c, void* dst, int dst_on_device, int dst_is_fp64) {
+  if (!c || !dst) return c ? fail(c, ROTGP_EINVAL, "null destination") : ROTGP_EINVAL;
+  const size_t pts = c->staging_bytes / 16;
+  const size_t bytes = pts * (dst_is_fp64 ? 16 : 8);
+  void* to = dst_on_device ? dst : c->staging;
+  cudaError_t e;
+  {
+    Timed t(c, K_IO);
+    e = launch_unpack(c->fp64, dst_is_fp64 != 0, c->psi[c->cur], to, c->nx, c->ny, c->nz,
+                      c->grid.dim, c->d_scale(), c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
+  if (!dst_on_device) {
+    e = cudaMemcpyAsync(dst, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy state to host");
+  }
+  return check_flags(c);
+}
+
+int rotgp_step_imag(rotgp_ctx* c, long long n) { return run_steps(c, n, true); }
+int rotgp_step_real(rotgp_ctx* c, long long n) { return run_steps(c, n, false); }
+
+int rotgp_observables(rotgp_ctx* c, rotgp_obs* out) {
+  if (!c || !out) return c ? fail(c, ROTGP_EINVAL, "null output") : ROTGP_EINVAL;
+  obs_args a{};
+  a.psi = c->psi[c->cur];
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.dim = c->grid.dim;
+  a.hx = c->grid.h[0];
+  a.hy = c->grid.h[1];
+  a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
+  a.x0 = c->x0;
+  a.y0 = c->y0;
+  a.z0 = c->z0;
+  a.hgam2 = 0.5 * c->phys.gamma * c->phys.gamma;
+  a.hnu2 = 0.5 * c->phys.nu * c->phys.nu;
+  a.hlam2 = c->grid.dim == 3 ? 0.5 * c->phys.lambda * c->phys.lambda : 0.0;
+  a.g = c->phys.g;
+  a.omega = c->phys.omega;
+  a.scale = c->d_scale();
+  a.partials = c->partials;
+  a.counter = c->counter;
+  a.result = c->d_obs();
+  cudaError_t e;
+  {
+    Timed t(c, K_OBS);
+    e = launch_observables(c->fp64, a, reduce_blocks(c, c->sites), 256, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "observables kernel");
+  vort_args v{};
+  v.psi = c->psi[c->cur];
+  v.nx = c->nx;
+  v.ny = c->ny;
+  v.nz = c->nz;
+  v.dim = c->grid.dim;
+  v.kplane = c->grid.dim == 3 ? c->grid.n[2] / 2 : 0;
+  v.hx = c->grid.h[0];
+  v.hy = c->grid.h[1];
+  v.x0 = c->x0;
+  v.y0 = c->y0;
+  v.partials = c->partials;
+  v.counter = c->counter;
+  v.moments = c->d_moments();
+  v.count = c->d_count();
+  const int vb = reduce_blocks(c, (long long)c->nx * c->ny);
+  {
+    Timed t(c, K_VMOM);
+    e = launch_vortex_moments(c->fp64, v, vb, 256, c->stream);
+  }
+  if (e == cudaSuccess) {
+    Timed t(c, K_VCOUNT);
+    e = launch_vortex_count(c->fp64, v, vb, 256, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "vortex kernels");
+  e = cudaMemcpyAsync(c->h_obs, c->d_obs(), NOBS * sizeof(double), cudaMemcpyDeviceToHost,
+                      c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_obs + NOBS, c->d_count(), sizeof(int), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy observables");
+  int rc = check_flags(c);
+  if (rc) return rc;
+  const double* r = c->h_obs;
+  out->norm = r[0];
+  out->mu = r[1];
+  out->energy = r[2];
+  out->mu_c = r[3];
+  out->energy_c = r[4];
+  out->rms_x = r[5];
+  out->rms_y = r[6];
+  out->rms_z = r[7];
+  out->rms_r = r[8];
+  out->max_density = r[9];
+  int cnt = 0;
+  std::memcpy(&cnt, c->h_obs + NOBS, sizeof(int));
+  out->vortices = cnt;
+  out->step = c->steps;
+  out->flags = c->phys.omega >= std::min(c->phys.gamma, c->phys.nu) ? 1 : 0;
+  return ROTGP_OK;
+}
+
+int rotgp_sync(rotgp_ctx* c) {
+  if (!c) return ROTGP_EINVAL;
+  return check_flags(c);
+}
+
+int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
+  if (!c || !out) return ROTGP_EINVAL;
+  out->precision = c->prec;
+  out->halo = c->halo;
+  out->chunk_x = c->chunk_x;
+  out->chunk_s = c->chunk_s;
+  out->table_len = c->lt;
+  out->decay = c->decay;
+  out->device_bytes = c->device_bytes;
+  return ROTGP_OK;
+}
+
+int rotgp_profile_enable(rotgp_ctx* c, int on) {
+  if (!c) return ROTGP_EINVAL;
+  c->prof = on != 0;
+  return ROTGP_OK;
+}
+
+int rotgp_profile_read(rotgp_ctx* c, rotgp_kstat* out, int max, int* count) {
+  if (!c || (!out && max > 0)) return ROTGP_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  long long n[K_COUNT] = {0};
+  double ms[K_COUNT] = {0};
+  for (auto& r : c->recs) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      n[r.kid] += 1;
+      ms[r.kid] += t;
+    }
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  int k = 0;
+  for (int id = 0; id < K_COUNT; ++id) {
+    if (!n[id]) continue;
+    if (k < max) {
+      std::memset(&out[k], 0, sizeof(rotgp_kstat));
+      std::snprintf(out[k].name, sizeof out[k].name, "%s", kKernelNames[id]);
+      out[k].launches = n[id];
+      out[k].total_ms = ms[id];
+      out[k].bytes_per_launch = c->bytes_per_launch[id];
+    }
+    ++k;
+  }
+  if (count) *count = std::min(k, max);
+  return ROTGP_OK;
+}
+
+}  // extern "C"

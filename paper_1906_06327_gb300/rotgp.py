@@ -1,0 +1,260 @@
+"""ctypes binding of ``librotgp.so`` (the C ABI of ``include/rotgp.h``).
+
+Argument marshalling only: every numerical step runs in the CUDA library.
+The library is loaded on first use and a missing or unloadable library is an
+error (there is no fallback).  Device memory and streams may come from
+PyTorch: pass ``torch.cuda.current_stream().cuda_stream`` as the stream and
+CUDA tensors as device buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ROTGP_OK = 0
+ROTGP_EINVAL = -1
+ROTGP_ENOMEM = -2
+ROTGP_ECUDA = -3
+ROTGP_ENONFINITE = -4
+ROTGP_EUNSUPPORTED = -5
+ROTGP_FP64 = 0
+ROTGP_FP32 = 1
+
+ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECUDA",
+               ROTGP_ENONFINITE: "ENONFINITE", ROTGP_EUNSUPPORTED: "EUNSUPPORTED"}
+
+# Every entry point declared in include/rotgp.h.
+EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
+           "rotgp_set_omega", "rotgp_init_analytic", "rotgp_set_psi", "rotgp_get_psi",
+           "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
+           "rotgp_info", "rotgp_profile_enable", "rotgp_profile_read")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3)]
+
+
+class Phys(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("gamma", "nu", "lam", "g", "omega", "dt")]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("norm", "mu", "energy", "mu_c", "energy_c",
+                                                "rms_x", "rms_y", "rms_z", "rms_r",
+                                                "max_density")] + \
+               [("step", ctypes.c_longlong), ("vortices", ctypes.c_int), ("flags", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double), ("bytes_per_launch", ctypes.c_double)]
+
+
+class SolverInfo(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("halo", ctypes.c_int), ("chunk_x", ctypes.c_int),
+                ("chunk_s", ctypes.c_int), ("table_len", ctypes.c_int),
+                ("decay", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+class RotgpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rotgp error {ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load librotgp.so (building it with nvcc if absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library missing: {path}")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+        lib.rotgp_create.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Phys), ip, vp,
+                                     ctypes.POINTER(vp)]
+        lib.rotgp_destroy.argtypes = [vp]
+        lib.rotgp_destroy.restype = None
+        lib.rotgp_last_error.argtypes = [vp]
+        lib.rotgp_last_error.restype = ctypes.c_char_p
+        lib.rotgp_set_phys.argtypes = [vp, ctypes.POINTER(Phys)]
+        lib.rotgp_set_omega.argtypes = [vp, ctypes.c_double]
+        lib.rotgp_init_analytic.argtypes = [vp, ip, dp, ctypes.c_double, ctypes.c_double]
+        lib.rotgp_set_psi.argtypes = [vp, vp, ip, ip]
+        lib.rotgp_get_psi.argtypes = [vp, vp, ip, ip]
+        lib.rotgp_step_imag.argtypes = [vp, ctypes.c_longlong]
+        lib.rotgp_step_real.argtypes = [vp, ctypes.c_longlong]
+        lib.rotgp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
+        lib.rotgp_sync.argtypes = [vp]
+        lib.rotgp_info.argtypes = [vp, ctypes.POINTER(SolverInfo)]
+        lib.rotgp_profile_enable.argtypes = [vp, ip]
+        lib.rotgp_profile_read.argtypes = [vp, ctypes.POINTER(KStat), ip, ctypes.POINTER(ip)]
+        _lib = lib
+        return lib
+
+
+def _shape(n) -> tuple:
+    return tuple(int(v) + 1 for v in reversed(n))
+
+
+class Solver:
+    """One condensate: ``rotgp_create`` ... ``rotgp_destroy``.
+
+    n: intervals per axis (2 or 3 values), h: spacings, precision "fp32" or
+    "fp64", stream: a cudaStream_t as int (0 = default stream).
+    """
+
+    def __init__(self, n, h, *, gamma=1.0, nu=1.0, lam=1.0, g=0.0, omega=0.0, dt=1e-3,
+                 precision="fp32", stream=0):
+        self._lib = load()
+        self.n, self.h = tuple(int(v) for v in n), tuple(float(v) for v in h)
+        self.dim = len(self.n)
+        self.fp64 = precision == "fp64"
+        grid = Grid(self.dim, (ctypes.c_int * 3)(*(list(self.n) + [0] * (3 - self.dim))),
+                    (ctypes.c_double * 3)(*(list(self.h) + [0.0] * (3 - self.dim))))
+        self.phys = Phys(gamma, nu, lam, g, omega, dt)
+        handle = ctypes.c_void_p()
+        rc = self._lib.rotgp_create(ctypes.byref(grid), ctypes.byref(self.phys),
+                                    ROTGP_FP64 if self.fp64 else ROTGP_FP32,
+                                    ctypes.c_void_p(int(stream)), ctypes.byref(handle))
+        if rc != ROTGP_OK:
+            raise RotgpError(rc, self._lib.rotgp_last_error(None).decode())
+        self._h = handle
+
+    # -- plumbing
+    def _check(self, rc: int):
+        if rc != ROTGP_OK:
+            raise RotgpError(rc, self._lib.rotgp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rotgp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self) -> tuple:
+        """Shape of an ABI wave function: (N_z+1,) (N_y+1, N_x+1)."""
+        return _shape(self.n)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # -- physics
+    def set_phys(self, **kw):
+        p = Phys(*[kw.get(k, getattr(self.phys, k)) for k, _ in Phys._fields_])
+        self._check(self._lib.rotgp_set_phys(self._h, ctypes.byref(p)))
+        self.phys = p
+
+    def set_omega(self, omega: float):
+        self._check(self._lib.rotgp_set_omega(self._h, float(omega)))
+        self.phys.omega = float(omega)
+
+    # -- state
+    def init_analytic(self, function: int = 1, phase_R=None, d_xy: float = 1.0, d_z: float = 1.0):
+        ptr = None
+        if phase_R is not None:
+            phase_R = np.ascontiguousarray(phase_R, dtype=np.float64)
+            if phase_R.shape != (self.n[1] + 1, self.n[0] + 1):
+                raise ValueError("phase_R must have shape (N_y+1, N_x+1)")
+            ptr = phase_R.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(self._lib.rotgp_init_analytic(self._h, int(function), ptr, float(d_xy),
+                                                  float(d_z)))
+
+    def set_psi(self, psi):
+        """psi: numpy complex64/complex128 array or a CUDA torch complex tensor."""
+        ptr, on_dev, is64, _keep = _buffer(psi, self.shape)
+        self._check(self._lib.rotgp_set_psi(self._h, ctypes.c_void_p(ptr), on_dev, is64))
+
+    def get_psi(self, out=None, fp64: bool = True):
+        """Return the state as numpy (or fill ``out``: numpy or CUDA torch tensor)."""
+        if out is None:
+            out = np.zeros(self.shape, dtype=np.complex128 if fp64 else np.complex64)
+        ptr, on_dev, is64, _keep = _buffer(out, self.shape)
+        self._check(self._lib.rotgp_get_psi(self._h, ctypes.c_void_p(ptr), on_dev, is64))
+        return out
+
+    # -- propagation
+    def step_imag(self, n: int = 1):
+        self._check(self._lib.rotgp_step_imag(self._h, int(n)))
+
+    def step_real(self, n: int = 1):
+        self._check(self._lib.rotgp_step_real(self._h, int(n)))
+
+    def observables(self) -> dict:
+        o = Obs()
+        self._check(self._lib.rotgp_observables(self._h, ctypes.byref(o)))
+        return o.as_dict()
+
+    def sync(self):
+        self._check(self._lib.rotgp_sync(self._h))
+
+    def info(self) -> dict:
+        i = SolverInfo()
+        self._check(self._lib.rotgp_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in SolverInfo._fields_}
+
+    # -- timing
+    def profile(self, on: bool = True):
+        self._check(self._lib.rotgp_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self) -> dict:
+        recs = (KStat * 16)()
+        cnt = ctypes.c_int(0)
+        self._check(self._lib.rotgp_profile_read(self._h, recs, 16, ctypes.byref(cnt)))
+        return {r.name.decode(): {"launches": r.launches, "total_ms": r.total_ms,
+                                  "bytes_per_launch": r.bytes_per_launch}
+                for r in recs[:cnt.value]}
+
+
+def _buffer(obj, shape):
+    """(pointer, on_device, is_fp64, keepalive) for numpy arrays / torch tensors."""
+    if isinstance(obj, np.ndarray):
+        if obj.dtype not in (np.complex64, np.complex128):
+            raise TypeError("state arrays must be complex64 or complex128")
+        if obj.shape != shape or not obj.flags.c_contiguous:
+            raise ValueError(f"state array must be C-contiguous with shape {shape}")
+        return obj.ctypes.data, 0, int(obj.dtype == np.complex128), obj
+    try:
+        import torch
+    except ImportError as e:  # pragma: no cover
+        raise TypeError("unsupported buffer type") from e
+    if isinstance(obj, torch.Tensor):
+        if obj.dtype not in (torch.complex64, torch.complex128):
+            raise TypeError("state tensors must be complex64 or complex128")
+        if tuple(obj.shape) != shape or not obj.is_contiguous():
+            raise ValueError(f"state tensor must be contiguous with shape {shape}")
+        return obj.data_ptr(), int(obj.is_cuda), int(obj.dtype == torch.complex128), obj
+    raise TypeError("unsupported buffer type")

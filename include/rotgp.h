@@ -100,12 +100,16 @@ typedef struct {
 /* Line-solver parameters of a context (rotgp_info). */
 typedef struct {
   int precision;
-  int halo;        /* H: halo points each chunk re-solves on either side   */
-  int chunk_x;     /* C: output points per chunk, x sweep                  */
-  int chunk_s;     /* C: output points per chunk, y and z sweeps           */
-  int table_len;   /* LU multiplier entries stored per line                */
-  double decay;    /* largest per-point decay factor of a truncated carry  */
-  size_t device_bytes; /* device memory owned by the context               */
+  int halo;               /* H: points over which a truncated line carry
+                             (forward or backward) is re-solved           */
+  int table_len;          /* coefficient entries stored per line          */
+  int chunk[3];           /* C: points per pipeline chunk, per axis       */
+  int segments[3];        /* independent segments each line is split into */
+  int lines_per_lane[3];  /* lines one GPU thread solves together         */
+  int ring[3];            /* chunk slots in flight per warp               */
+  int warps_per_block[3];
+  double decay;           /* largest per-point decay of a truncated carry */
+  size_t device_bytes;    /* device memory owned by the context           */
 } rotgp_solver_info;
 
 /* Create a context for one condensate on the current CUDA device; stream is
@@ -158,6 +162,17 @@ int rotgp_sync(rotgp_ctx* ctx);
 
 /* Line-solver parameters chosen for this context. */
 int rotgp_info(const rotgp_ctx* ctx, rotgp_solver_info* out);
+
+/* Launch shape of one sweep (axis 0 = x, 1 = y, 2 = z): lines solved per
+ * GPU thread (1, or 2 for complex float), chunk length C (8, 16 or 64;
+ * C >= the halo H of rotgp_info; complex float takes 8 or 16 with 2 lines
+ * per thread, 16 or 64 with one; double takes 16 or 64), ring slots (3 or
+ * 4), warps per block (1..8) and segments each line is split into (clamped
+ * to the number of chunks).  Changes speed only: every shape gives results
+ * equal up to the truncation bound of the chunked line solver.  Used by the
+ * autotuner.  ROTGP_EINVAL for a shape that is not built or does not fit. */
+int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring,
+               int warps_per_block, int segments);
 
 /* Per-kernel CUDA-event timing.  While enabled, every kernel launch of the
  * context is bracketed by events on its stream.  rotgp_profile_read

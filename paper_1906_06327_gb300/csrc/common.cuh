@@ -37,11 +37,17 @@ __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return mk(s * a.x, 
 template <class T>
 __device__ __forceinline__ T abs2(cpx<T> a) { return a.x * a.x + a.y * a.y; }
 
-// One entry of a line's LU multiplier table: for the unknown at index p,
-// m_p = 1 / (A0 - A- c'_{p-1}) and c'_p = A+ m_p (Thomas forward sweep).
+// Folded Thomas coefficients of one unknown p of one line (Eqs. eqD.11/eq5):
+// with m_p = 1/(A0 - A- c'_{p-1}) and c'_p = A+ m_p,
+//   forward   d'_p = a0 psi_p + am psi_{p-1} + ap psi_{p+1} + al d'_{p-1}
+//             a0 = m_p (1 - 2 kappa), am = m_p (kappa - tau), ap = m_p (kappa + tau),
+//             al = -m_p A-
+//   backward  x_p = d'_p + be x_{p+1},  be = -c'_p.
+// Entry 0 is all zero (the Dirichlet edge); entries past the table length
+// equal the last one (the Toeplitz fixed point).
 template <class T>
-struct __align__(4 * sizeof(T)) lu_entry {
-  cpx<T> c, m;
+struct __align__(16) coef5 {
+  cpx<T> a0, am, ap, al, be;
 };
 
 // Coefficients of one sweep axis in one propagation mode.  For a line with
@@ -56,35 +62,34 @@ struct axis_coef {
   double u0, du;          // u of line l is u0 + l du
 };
 
-// Arguments of a sweep kernel (both x and strided variants).
-struct sweep_args {
+// Arguments of a streaming line-sweep kernel.  A sweep solves nlines lines
+// of len points; each warp owns 32*V lines (V per lane) and one segment of
+// seg_chunks chunks of C points of them.
+struct stream_args {
   const void* in;
   void* out;
-  const void* table;  // lu_entry<T>[nlines_tab][lt + 1]
-  int nx, ny, nz;     // stored points per axis (nz = 1 in 2D)
-  int len;            // line length N_a (stored points)
-  long long stride;   // element stride along the line
-  long long ncols;    // number of lines
-  long long outer;    // strided: base(c) = (c / nx) * outer + c % nx
-  int chunk, halo, lt, nchunks, pitch;
-  axis_coef co;
-  int tab_mod;        // table line index = (line index for coef) ; see kernels
-  // H1 fused into the x sweep
-  int h1;
-  double dt;          // Delta
-  double g;
-  double hgam2, hnu2, hlam2;  // gamma^2/2, nu^2/2, lambda^2/2
-  double x0, hx, y0, hy, z0, hz;  // coordinates: x_i = x0 + i hx etc.
-  const double* scale;  // pending scale applied at load (x sweep)
-  // norm epilogue of the last sweep
-  int reduce;
-  double vol;         // h_x h_y [h_z]
+  const void* coef;   // coef5<T>[coefficient lines][lt + 1]
+  int len;            // N: stored points per line
+  int lt;             // index of the converged table entry
+  int nseg, seg_chunks, warm, halo;
+  int ring;           // slots of the per-warp chunk ring (3 or 4)
+  long long nlines;
+  // strided lines (y, z): line c starts at (c / nx) * outer + c % nx, step stride
+  int nx, ny;
+  long long stride, outer;
+  int coef_mode;      // 0: one coefficient line (z); 1: c % nx (y); 2: row % ny (x)
+  // H1 substep fused into the x sweep
+  double dt, g, hgam2, hnu2, hlam2;
+  double x0, hx, y0, hy, z0, hz;
+  const double* scale;  // pending renormalisation applied as the state is read
+  // norm reduction in the last sweep of a step
+  double vol;
   int imag;
-  double* partials;   // per-block partial sums
+  double* partials;
   unsigned int* counter;
-  double* scale_out;  // new pending scale
+  double* scale_out;
   double* norm_out;
-  int* flags;         // bit 0: non-finite norm
+  int* flags;
 };
 
 struct obs_args {
@@ -112,12 +117,29 @@ struct vort_args {
 };
 
 // ---- launchers (one per translation unit group); return cudaGetLastError
+// Launch shape of one sweep, chosen on the host.
+struct sweep_shape {
+  int V;          // lines per lane (1 or 2)
+  int C;          // chunk length (8, 16 or 64)
+  int R;          // ring slots (3 or 4)
+  bool vec16;     // x sweep: 16-byte copies (even row length)
+  int warps_per_block;
+  long long blocks;
+  size_t smem;
+};
+
 cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis_coef& co,
                           cudaStream_t s);
-cudaError_t launch_sweep_x(bool fp64, bool imag, const sweep_args& a, int blocks, int threads,
-                           size_t smem, cudaStream_t s);
-cudaError_t launch_sweep_strided(bool fp64, const sweep_args& a, int blocks, int cols_per_block,
-                                 int chunks_per_block, size_t smem, cudaStream_t s);
+cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,
+                           cudaStream_t s);
+cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
+                                 const sweep_shape& sh, cudaStream_t s);
+size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);
+// Is (precision, V, C) one of the instantiated sweep kernels?
+inline bool sweep_shape_built(bool fp64, int V, int C) {
+  if (fp64) return V == 1 && (C == 16 || C == 64);
+  return (V == 2 && (C == 8 || C == 16)) || (V == 1 && (C == 16 || C == 64));
+}
 cudaError_t launch_observables(bool fp64, const obs_args& a, int blocks, int threads,
                                cudaStream_t s);
 cudaError_t launch_vortex_moments(bool fp64, const vort_args& a, int blocks, int threads,

@@ -35,6 +35,11 @@ struct AxisPlan {
   int nlines = 0;       // lines with distinct coefficients (table rows)
   axis_coef co[2];      // [mode] 0 = real, 1 = imaginary
   void* table[2] = {nullptr, nullptr};
+  // launch plan of this axis' sweep
+  long long lines = 0;  // lines solved per sweep
+  int len = 0;          // points per line
+  int nseg = 1, seg_chunks = 1, warm = 1;
+  sweep_shape sh{};
 };
 
 struct ProfRec {
@@ -55,9 +60,8 @@ struct rotgp_ctx {
   size_t elem = 8;
   double x0 = 0, y0 = 0, z0 = 0, vol = 1;
   // solver sizing
-  int halo = 2, chunk_x = 32, chunk_s = 32, lt = 8;
+  int halo = 2, lt = 8;
   double decay = 0;
-  int warps_x = 4, pitch_x = 0, cpb_s = 4;
   // device memory
   void* psi[2] = {nullptr, nullptr};
   int cur = 0;
@@ -190,30 +194,65 @@ int plan_solver(rotgp_ctx* c, int* halo, int* lt, double* decay) {
   return ROTGP_OK;
 }
 
-int choose_layout(rotgp_ctx* c) {
-  const int H = c->halo;
-  const int C = H <= 8 ? 32 : 64;
-  c->chunk_x = C;
-  c->chunk_s = C;
-  const int W = C + 2 * H + 2;
-  c->pitch_x = (W % 2) ? W : W + 1;
-  const size_t limit = (size_t)c->smem_optin - 1024;  // static shared memory reserve
-  const size_t per_warp = (size_t)32 * c->pitch_x * c->elem;
-  c->warps_x = 4;
-  while (c->warps_x > 1 && per_warp * c->warps_x > limit) c->warps_x /= 2;
-  if (per_warp > limit) return fail(c, ROTGP_EUNSUPPORTED, "x tile too large");
-  const size_t per_s = (size_t)32 * W * c->elem;
-  c->cpb_s = 4;
-  while (c->cpb_s > 1 && per_s * c->cpb_s > limit) c->cpb_s /= 2;
-  if (per_s > limit) return fail(c, ROTGP_EUNSUPPORTED, "strided tile too large");
+// Set the launch shape of axis a: V lines per lane, chunk C, R ring slots,
+// wpb warps per block, nseg segments per line; recompute blocks and shared
+// memory.  Only shapes with an instantiated kernel are accepted.
+int set_shape(rotgp_ctx* c, int a, int V, int C, int R, int wpb, long long nseg) {
+  AxisPlan& ap = c->axis[a];
+  const bool x = a == 0;
+  const size_t limit = (size_t)c->smem_optin - 1024;
+  if (!sweep_shape_built(c->fp64, V, C))
+    return fail(c, ROTGP_EINVAL, "no sweep kernel for %d lines per lane and chunk %d", V, C);
+  if (V == 2 && !x && c->nx % 2 != 0)
+    return fail(c, ROTGP_EINVAL, "two lines per lane in y/z sweeps need an even N_x");
+  if (C < c->halo) return fail(c, ROTGP_EINVAL, "chunk %d shorter than the halo %d", C, c->halo);
+  if (R != 3 && R != 4) return fail(c, ROTGP_EINVAL, "ring must have 3 or 4 slots");
+  const size_t per_warp = sweep_smem_per_warp(c->fp64, x, V, C, R);
+  if (per_warp * wpb > limit) return fail(c, ROTGP_EINVAL, "launch shape exceeds shared memory");
+  const int nch = (ap.len + C - 1) / C;
+  nseg = std::max<long long>(1, std::min<long long>(nseg, nch));
+  ap.seg_chunks = (int)((nch + nseg - 1) / nseg);
+  ap.nseg = (nch + ap.seg_chunks - 1) / ap.seg_chunks;
+  ap.warm = (c->halo + 1 + C - 1) / C;
+  ap.sh.V = V;
+  ap.sh.C = C;
+  ap.sh.R = R;
+  ap.sh.vec16 = c->fp64 || (x && c->nx % 2 == 0);
+  ap.sh.warps_per_block = wpb;
+  ap.sh.smem = per_warp * wpb;
+  const long long groups = (ap.lines + 32 * V - 1) / (32 * V);
+  ap.sh.blocks = (groups * ap.nseg + wpb - 1) / wpb;
   return ROTGP_OK;
 }
 
-long long strided_blocks(const rotgp_ctx* c, int axis) {
-  const long long ncols = axis == 1 ? (long long)c->nx * c->nz : (long long)c->nx * c->ny;
-  const int len = axis == 1 ? c->ny : c->nz;
-  const int nch = (len + c->chunk_s - 1) / c->chunk_s;
-  return ((ncols + 31) / 32) * ((nch + c->cpb_s - 1) / c->cpb_s);
+// Default launch plan of every sweep: complex float solves two lines per
+// lane in chunks of 8 (16 if the halo is longer), double one line in chunks
+// of 16 (64); a 3-slot ring; one warp per block, so that blocks of ~15 KB
+// pack each SM densely; and enough segments per line for about one wave of
+// resident warps.
+int plan_axes(rotgp_ctx* c) {
+  const size_t sm_bytes = 228 * 1024;
+  for (int a = 0; a < c->grid.dim; ++a) {
+    AxisPlan& ap = c->axis[a];
+    const bool x = a == 0;
+    ap.len = a == 0 ? c->nx : (a == 1 ? c->ny : c->nz);
+    ap.lines = a == 0 ? (long long)c->ny * c->nz
+                      : (a == 1 ? (long long)c->nx * c->nz : (long long)c->nx * c->ny);
+    int V = 1, C = c->halo <= 16 ? 16 : 64;
+    if (!c->fp64 && c->halo <= 16 && (x || c->nx % 2 == 0)) {
+      V = 2;
+      C = c->halo <= 8 ? 8 : 16;
+    }
+    const int R = 3;
+    const size_t per_warp = sweep_smem_per_warp(c->fp64, x, V, C, R);
+    const long long resident =
+        std::max<long long>(1, std::min<long long>(32, (long long)(sm_bytes / (per_warp + 1024))));
+    const long long target = resident * c->sm_count;
+    const long long groups = (ap.lines + 32 * V - 1) / (32 * V);
+    int rc = set_shape(c, a, V, C, R, 1, std::max<long long>(1, target / groups));
+    if (rc) return rc == ROTGP_EINVAL ? fail(c, ROTGP_EUNSUPPORTED, "%s", c->err.c_str()) : rc;
+  }
+  return ROTGP_OK;
 }
 
 int reduce_blocks(const rotgp_ctx* c, long long n) {
@@ -271,16 +310,21 @@ int build_tables(rotgp_ctx* c) {
 // --------------------------------------------------------------- one step
 int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
   const int mode = imag ? 1 : 0;
-  sweep_args a{};
+  const AxisPlan& ap = c->axis[axis];
+  stream_args a{};
   a.in = c->psi[c->cur];
   a.out = c->psi[1 - c->cur];
-  a.table = c->axis[axis].table[mode];
+  a.coef = ap.table[mode];
+  a.len = ap.len;
+  a.lt = c->lt;
+  a.nseg = ap.nseg;
+  a.seg_chunks = ap.seg_chunks;
+  a.warm = ap.warm;
+  a.halo = c->halo;
+  a.ring = ap.sh.R;
+  a.nlines = ap.lines;
   a.nx = c->nx;
   a.ny = c->ny;
-  a.nz = c->nz;
-  a.halo = c->halo;
-  a.lt = c->lt;
-  a.co = c->axis[axis].co[mode];
   a.vol = c->vol;
   a.imag = imag ? 1 : 0;
   a.partials = c->partials;
@@ -290,12 +334,7 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
   a.flags = c->d_flags();
   cudaError_t e;
   if (axis == 0) {
-    a.len = c->nx;
-    a.stride = 1;
-    a.chunk = c->chunk_x;
-    a.nchunks = (c->nx + c->chunk_x - 1) / c->chunk_x;
-    a.pitch = c->pitch_x;
-    a.h1 = 1;
+    a.coef_mode = 2;
     a.dt = c->phys.dt;
     a.g = c->phys.g;
     a.hgam2 = 0.5 * c->phys.gamma * c->phys.gamma;
@@ -308,26 +347,14 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.z0 = c->z0;
     a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
     a.scale = c->d_scale();
-    const long long rows = (long long)c->ny * c->nz;
-    const long long tiles = ((rows + 31) / 32) * a.nchunks;
-    const int blocks = (int)((tiles + c->warps_x - 1) / c->warps_x);
-    const size_t smem = (size_t)c->warps_x * 32 * c->pitch_x * c->elem;
     Timed t(c, K_SWEEP_X);
-    e = launch_sweep_x(c->fp64, imag, a, blocks, 32 * c->warps_x, smem, c->stream);
+    e = launch_sweep_x(c->fp64, imag, a, ap.sh, c->stream);
   } else {
-    a.len = axis == 1 ? c->ny : c->nz;
     a.stride = axis == 1 ? (long long)c->nx : (long long)c->nx * c->ny;
-    a.ncols = axis == 1 ? (long long)c->nx * c->nz : (long long)c->nx * c->ny;
     a.outer = axis == 1 ? (long long)c->nx * c->ny : (long long)c->nx;
-    a.tab_mod = axis == 1 ? 1 : 0;
-    a.chunk = c->chunk_s;
-    a.nchunks = (a.len + c->chunk_s - 1) / c->chunk_s;
-    a.reduce = last ? 1 : 0;
-    const int W = c->chunk_s + 2 * c->halo + 2;
-    const size_t smem = (size_t)c->cpb_s * 32 * W * c->elem;
-    const int gx = (int)((a.ncols + 31) / 32);
+    a.coef_mode = axis == 1 ? 1 : 0;
     Timed t(c, axis == 1 ? K_SWEEP_Y : K_SWEEP_Z);
-    e = launch_sweep_strided(c->fp64, a, gx, 32, c->cpb_s, smem, c->stream);
+    e = launch_sweep_strided(c->fp64, last, a, ap.sh, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
   c->cur = 1 - c->cur;
@@ -353,6 +380,7 @@ int check_flags(rotgp_ctx* c) {
                                   c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+  if (flags & 2) return fail(c, ROTGP_ECUDA, "a sweep kernel was launched with a shape it was not built for");
   if (flags & 1) return fail(c, ROTGP_ENONFINITE, "non-finite or zero norm in a reduction");
   return ROTGP_OK;
 }
@@ -445,7 +473,7 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     return rc;
   }
   int rc = plan_solver(c, &c->halo, &c->lt, &c->decay);
-  if (!rc) rc = choose_layout(c);
+  if (!rc) rc = plan_axes(c);
   if (rc) {
     g_create_error = c->err;
     delete c;
@@ -456,13 +484,19 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
   c->axis[2].nlines = 1;
   // reduction scratch: the largest per-block partial count of any reduction
   size_t pd = (size_t)reduce_blocks(c, c->sites) * NQ;
-  for (int a = 1; a < grid->dim; ++a) pd = std::max(pd, (size_t)strided_blocks(c, a));
+  {
+    // largest block count any launch shape of the last sweep can take:
+    // one warp per block, one line per lane, one segment per chunk
+    const AxisPlan& last = c->axis[grid->dim - 1];
+    const long long nch = (last.len + 15) / 16;
+    pd = std::max(pd, (size_t)(((last.lines + 31) / 32) * nch));
+  }
   pd = std::max(pd, (size_t)reduce_blocks(c, (long long)c->nx * c->ny) * 3);
   c->partial_doubles = pd;
   c->staging_bytes = (size_t)(grid->n[0] + 1) * (grid->n[1] + 1) *
                      (grid->dim == 3 ? grid->n[2] + 1 : 1) * 16;
   const size_t state = (size_t)c->sites * c->elem;
-  const size_t tab_elem = c->fp64 ? sizeof(lu_entry<double>) : sizeof(lu_entry<float>);
+  const size_t tab_elem = c->fp64 ? sizeof(coef5<double>) : sizeof(coef5<float>);
   rc = dev_alloc(c, &c->psi[0], state);
   if (!rc) rc = dev_alloc(c, &c->psi[1], state);
   if (!rc) rc = dev_alloc(c, &c->staging, c->staging_bytes);
@@ -527,16 +561,12 @@ int rotgp_set_phys(rotgp_ctx* c, const rotgp_phys* phys) {
   if (!rc && halo > c->halo) {
     const int old_h = c->halo;
     c->halo = halo;
-    rc = choose_layout(c);
-    if (!rc) {
-      // partial buffer size depends on the strided launch shape
-      for (int a = 1; a < c->grid.dim; ++a)
-        if ((size_t)strided_blocks(c, a) > c->partial_doubles)
-          rc = fail(c, ROTGP_EUNSUPPORTED, "new physics needs a larger reduction buffer");
-    }
+    rc = plan_axes(c);
+    if (!rc && (size_t)c->axis[c->grid.dim - 1].sh.blocks > c->partial_doubles)
+      rc = fail(c, ROTGP_EUNSUPPORTED, "new physics needs a larger reduction buffer");
     if (rc) {
       c->halo = old_h;
-      choose_layout(c);
+      plan_axes(c);
     }
   }
   if (rc) {
@@ -724,12 +754,31 @@ int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
   if (!c || !out) return ROTGP_EINVAL;
   out->precision = c->prec;
   out->halo = c->halo;
-  out->chunk_x = c->chunk_x;
-  out->chunk_s = c->chunk_s;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < c->grid.dim;
+    out->chunk[a] = on ? c->axis[a].sh.C : 0;
+    out->segments[a] = on ? c->axis[a].nseg : 0;
+    out->lines_per_lane[a] = on ? c->axis[a].sh.V : 0;
+    out->ring[a] = on ? c->axis[a].sh.R : 0;
+    out->warps_per_block[a] = on ? c->axis[a].sh.warps_per_block : 0;
+  }
   out->table_len = c->lt;
   out->decay = c->decay;
   out->device_bytes = c->device_bytes;
   return ROTGP_OK;
+}
+
+int rotgp_tune(rotgp_ctx* c, int axis, int lines_per_lane, int chunk, int ring,
+               int warps_per_block, int segments) {
+  if (!c) return ROTGP_EINVAL;
+  if (axis < 0 || axis >= c->grid.dim) return fail(c, ROTGP_EINVAL, "axis out of range");
+  if (warps_per_block < 1 || warps_per_block > 8)
+    return fail(c, ROTGP_EINVAL, "warps_per_block must be 1..8");
+  if (segments < 1) return fail(c, ROTGP_EINVAL, "segments must be >= 1");
+  const AxisPlan keep = c->axis[axis];
+  int rc = set_shape(c, axis, lines_per_lane, chunk, ring, warps_per_block, segments);
+  if (rc) c->axis[axis] = keep;
+  return rc;
 }
 
 int rotgp_profile_enable(rotgp_ctx* c, int on) {

@@ -1,0 +1,320 @@
+// sweep_s.cu -- the strided line sweeps of one split step: H3 along y
+// (Eq. eq3, "performed similarly" to Eq. eqD.9) and the z sweep of the 3D
+// "identical prescription", with the norm of the state reduced in the last
+// sweep of a step; and the per-line coefficient tables of every sweep.
+//
+// y and z lines are strided: lane = adjacent columns, so every copy of a
+// warp covers 32*V consecutive points, each lane keeps its own column in a
+// [point][lane] slab of the ring (no bank conflicts, no cross-lane sharing)
+// and stores its results straight to global memory, coalesced.  The solver
+// and the ring are described in sweep_common.cuh.
+#include "sweep_common.cuh"
+
+namespace rotgp {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-thread sum of |x|^2: Kahan-compensated in float, plain in double.
+template <class T>
+struct acc_t {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T v) {
+    T y = v - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <>
+struct acc_t<double> {
+  double s = 0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// Block sum of v -> per-block partial; the last block to finish sums the
+// partials in block order (deterministic), sets the norm, the pending scale
+// (1/sqrt(norm) in imaginary time, 1 in real time) and the non-finite flag.
+__device__ void norm_epilogue(double v, const stream_args& a) {
+  __shared__ double ws[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned nblocks = gridDim.x;
+  v = warp_sum(v);
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += ws[w];
+    a.partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned t = atomicAdd(a.counter, 1u);
+    last = (t == nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0;
+  for (unsigned i = threadIdx.x; i < nblocks; i += blockDim.x) s += __ldcg(&a.partials[i]);
+  s = warp_sum(s);
+  __syncthreads();
+  if (lane == 0) ws[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0;
+    for (int w = 0; w < nw; ++w) tot += ws[w];
+    double n = tot * a.vol;
+    *a.norm_out = n;
+    if (!(n > 0.0) || !isfinite(n)) {
+      atomicOr(a.flags, 1);
+      *a.scale_out = 1.0;
+    } else {
+      *a.scale_out = a.imag ? 1.0 / sqrt(n) : 1.0;
+    }
+    *a.counter = 0u;
+  }
+}
+
+// --------------------------------------------------------------- tables
+// Thomas multipliers of one line, m_1 = 1/A0, c'_1 = A+ m_1,
+// m_p = 1/(A0 - A- c'_{p-1}), c'_p = A+ m_p, folded into coef5 entries
+// p = 1..lt (computed in double); entry 0 is zero.
+struct dcx {
+  double x, y;
+};
+__device__ __forceinline__ dcx dmul(dcx a, dcx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ dcx dsub(dcx a, dcx b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ dcx dinv(dcx a) {
+  const double r = 1.0 / (a.x * a.x + a.y * a.y);
+  return {a.x * r, -a.y * r};
+}
+template <class T>
+__device__ __forceinline__ cpx<T> dcast(dcx a) { return mk<T>((T)a.x, (T)a.y); }
+
+template <class T>
+__global__ void k_tables(coef5<T>* tab, int nlines, int lt, axis_coef co) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nlines) return;
+  const double u = co.u0 + (double)l * co.du;
+  const dcx kap{co.kap_re, co.kap_im}, tau{co.tau_re * u, co.tau_im * u};
+  const dcx one{1.0, 0.0};
+  const dcx a0{1.0 + 2.0 * kap.x, 2.0 * kap.y};
+  const dcx am = dsub(tau, kap), ap{-kap.x - tau.x, -kap.y - tau.y};
+  const dcx diag = dsub(one, {2.0 * kap.x, 2.0 * kap.y});
+  const dcx kmt = dsub(kap, tau), kpt{kap.x + tau.x, kap.y + tau.y};
+  coef5<T>* t = tab + (size_t)l * (lt + 1);
+  t[0].a0 = t[0].am = t[0].ap = t[0].al = t[0].be = zero<T>();
+  dcx c{0.0, 0.0};
+  for (int p = 1; p <= lt; ++p) {
+    const dcx m = dinv(dsub(a0, dmul(am, c)));
+    c = dmul(ap, m);
+    t[p].a0 = dcast<T>(dmul(m, diag));
+    t[p].am = dcast<T>(dmul(m, kmt));
+    t[p].ap = dcast<T>(dmul(m, kpt));
+    const dcx mam = dmul(m, am);
+    t[p].al = dcast<T>({-mam.x, -mam.y});
+    t[p].be = dcast<T>({-c.x, -c.y});
+  }
+}
+
+// --------------------------------------------------------------- y / z sweeps
+// Forward sweep over one chunk slot (C+1 packs, stride 32 between points):
+// psi -> d' in place for the first C points.
+template <class T, int V, int C, bool FAST>
+__device__ __forceinline__ void strided_forward(pack<T, V>* s0, cpx<T> (&pm)[V], cpx<T> (&d)[V],
+                                                const coef5<T>* const (&crow)[V],
+                                                const coef5<T> (&cinf)[V], int p0, int lt) {
+  pack<T, V> cur = s0[0];
+#pragma unroll(unroll_of<C>::value)
+  for (int r = 0; r < C; ++r) {
+    const pack<T, V> nx = s0[(r + 1) * 32];
+    pack<T, V> o;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d[v] = fwd(coef_at<T, FAST>(crow[v], cinf[v], p0 + r, lt), pm[v], cur.v[v], nx.v[v], d[v]);
+      pm[v] = cur.v[v];
+      o.v[v] = d[v];
+    }
+    s0[r * 32] = o;
+    cur = nx;
+  }
+}
+
+template <class T, int V, int C, bool REDUCE>
+__global__ void __launch_bounds__(128) k_sweep_strided(const stream_args a) {
+  using E = cpx<T>;
+  using Pk = pack<T, V>;
+  constexpr int SLOT = (C + 1) * 32;  // packs per ring slot
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int R = a.ring;
+  // a launch whose shared memory does not match this instantiation flags an
+  // error and does nothing (uniform over the block)
+  if (R < 3 || R > 4 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT) * (unsigned)sizeof(Pk)) {
+    if (threadIdx.x == 0) atomicOr(a.flags, 2);
+    return;
+  }
+  Pk* ring = reinterpret_cast<Pk*>(smem_raw) + (size_t)wib * R * SLOT;
+  const long long ngroups = (a.nlines + 32 * V - 1) / (32 * V);
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  acc_t<T> acc;
+  if (wg < ngroups * a.nseg) {
+    const long long g = wg % ngroups;
+    const int sg = (int)(wg / ngroups);
+    const long long c0 = (g * 32 + lane) * V;
+    const bool active = c0 < a.nlines;
+    const long long base = active ? (c0 / a.nx) * a.outer + (c0 % a.nx) : 0;
+    const E* in = static_cast<const E*>(a.in) + base;
+    E* out = static_cast<E*>(a.out) + base;
+    const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
+    const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
+    const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
+    const coef5<T>* crow[V];
+    coef5<T> cinf[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int li = (a.coef_mode == 1 && active) ? (int)((c0 + v) % a.nx) : 0;
+      crow[v] = static_cast<const coef5<T>*>(a.coef) + (size_t)li * (lt + 1);
+      cinf[v] = crow[v][lt];
+    }
+    auto slot = [&](int q) { return ring + (size_t)(q % R) * SLOT + lane; };
+    // copy points q*C .. q*C + C of this lane's lines (zero past the line)
+    auto issue = [&](int q) {
+      if (q < qb) {
+        Pk* s = slot(q);
+#pragma unroll
+        for (int r = 0; r <= C; ++r) {
+          const int p = q * C + r;
+          if (active && p < N)
+            cp_async<sizeof(Pk)>(&s[r * 32], in + (long long)p * a.stride);
+          else
+            s[r * 32] = Pk{};
+        }
+      }
+      cp_async_commit();
+    };
+    for (int i = 0; i < R - 1; ++i) issue(qa + i);
+    E pm[V], d[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) pm[v] = d[v] = zero<T>();
+    for (int q = qa; q <= qb; ++q) {
+      if (q < qb) {
+        ring_wait(R);
+        if (q * C >= lt && (q + 1) * C <= N)
+          strided_forward<T, V, C, true>(slot(q), pm, d, crow, cinf, q * C, lt);
+        else
+          strided_forward<T, V, C, false>(slot(q), pm, d, crow, cinf, q * C, lt);
+      }
+      const int qq = q - 1;
+      if (qq >= qo0 && qq < qo1) {
+        E x[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = zero<T>();
+        // H points of look-ahead into chunk q (truncated start), or the exact
+        // start at the last unknown N-1 when the line ends first
+        const int la = min(a.halo, N - q * C);
+        const Pk* sq = slot(q);
+        for (int h = la - 1; h >= 0; --h) {
+          const Pk t = sq[h * 32];
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const E be = crow[v][min(q * C + h, lt)].be;
+            x[v] = cfma(be, x[v], t.v[v]);
+          }
+        }
+        const Pk* sp = slot(qq);
+        const bool fast = qq * C >= lt && q * C <= N;
+        auto back = [&](auto fast_tag) {
+          constexpr bool FAST = decltype(fast_tag)::value;
+#pragma unroll(unroll_of<C>::value)
+          for (int r = C - 1; r >= 0; --r) {
+            const int p = qq * C + r;
+            if (!FAST && p >= N) continue;
+            const Pk t = sp[r * 32];
+            Pk o;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              x[v] = cfma(coef_at<T, FAST>(crow[v], cinf[v], p, lt).be, x[v], t.v[v]);
+              o.v[v] = x[v];
+              if (REDUCE) acc.add(abs2(x[v]));
+            }
+            if (active) *reinterpret_cast<Pk*>(out + (long long)p * a.stride) = o;
+          }
+        };
+        if (fast)
+          back(bool_tag<true>{});
+        else
+          back(bool_tag<false>{});
+      }
+      issue(q + R - 1);
+    }
+    cp_async_wait<0>();
+  }
+  if (REDUCE) norm_epilogue(acc.value(), a);
+}
+
+// --------------------------------------------------------------- launchers
+cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis_coef& co,
+                          cudaStream_t s) {
+  const int threads = 128, blocks = (nlines + threads - 1) / threads;
+  if (fp64)
+    k_tables<double><<<blocks, threads, 0, s>>>(static_cast<coef5<double>*>(table), nlines, lt, co);
+  else
+    k_tables<float><<<blocks, threads, 0, s>>>(static_cast<coef5<float>*>(table), nlines, lt, co);
+  return cudaGetLastError();
+}
+
+size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R) {
+  const size_t e = fp64 ? 16 : 8;
+  if (x_sweep) return (size_t)R * (32 * V) * (fp64 ? C + 1 : C + 2) * e;
+  return (size_t)R * (C + 1) * 32 * V * e;
+}
+
+cudaError_t allow_smem(const void* fn, bool* done) {
+  if (*done) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) *done = true;
+  return e;
+}
+
+template <class T, int V, int C>
+static cudaError_t dispatch_s(bool reduce, const stream_args& a, const sweep_shape& sh,
+                              cudaStream_t s) {
+  static bool done[2] = {false, false};
+  auto fn = reduce ? k_sweep_strided<T, V, C, true> : k_sweep_strided<T, V, C, false>;
+  cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Every (precision, V, C) combination the host can choose is instantiated
+// here; anything else is rejected before a launch.
+cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
+                                 const sweep_shape& sh, cudaStream_t s) {
+  if (fp64) {
+    if (sh.V == 1 && sh.C == 16) return dispatch_s<double, 1, 16>(reduce, a, sh, s);
+    if (sh.V == 1 && sh.C == 64) return dispatch_s<double, 1, 64>(reduce, a, sh, s);
+    return cudaErrorInvalidValue;
+  }
+  if (sh.V == 2 && sh.C == 8) return dispatch_s<float, 2, 8>(reduce, a, sh, s);
+  if (sh.V == 2 && sh.C == 16) return dispatch_s<float, 2, 16>(reduce, a, sh, s);
+  if (sh.V == 1 && sh.C == 16) return dispatch_s<float, 1, 16>(reduce, a, sh, s);
+  if (sh.V == 1 && sh.C == 64) return dispatch_s<float, 1, 64>(reduce, a, sh, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace rotgp

@@ -1,0 +1,256 @@
+// sweep_x.cu -- the x sweep of one split step: the H1 substep (Eq. eq1,
+// exact pointwise solution) fused into the Crank-Nicolson solve of H2
+// (Eq. eq2, discretised as Eq. eqD.9 with the coefficients of Eqs.
+// eqD.11/eq5), with the pending imaginary-time renormalisation applied as
+// the state is read.
+//
+// x lines are contiguous: the warp copies 32*V rows x (C + 1) points of a
+// chunk cooperatively (coalesced 8- or 16-byte copies) into rows padded to
+// an odd number of 16-byte units; each lane then walks its own V rows with
+// 16-byte shared loads (conflict-free) and the results go back through the
+// same slot for coalesced stores.  The solver and the ring are described in
+// sweep_common.cuh.
+#include "sweep_common.cuh"
+
+namespace rotgp {
+
+cudaError_t allow_smem(const void* fn, bool* done);
+
+template <class T, int V, int C, bool IMAG, bool VEC16>
+__global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
+  using E = cpx<T>;
+  constexpr bool F32 = sizeof(T) == 4;
+  constexpr int EP = (F32 && VEC16) ? 2 : 1;          // points per copy
+  constexpr int PITCH = F32 ? C + 2 : C + 1;           // odd number of 16-byte units
+  constexpr int ROWS = 32 * V;
+  constexpr int SLOT = ROWS * PITCH;
+  constexpr int LPR = (C + 1 + EP - 1) / EP;           // copies per row (chunk + 1 point)
+  constexpr int SPR = C / EP;                          // stores per row
+  static_assert(LPR * EP <= PITCH, "row pitch too small");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int R = a.ring;
+  if (R < 3 || R > 4 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT) * (unsigned)sizeof(E)) {
+    if (threadIdx.x == 0) atomicOr(a.flags, 2);
+    return;
+  }
+  E* ring = reinterpret_cast<E*>(smem_raw) + (size_t)wib * R * SLOT;
+  const long long nrows = a.nlines;
+  const long long ngroups = (nrows + ROWS - 1) / ROWS;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= ngroups * a.nseg) return;  // whole warp; no block barrier below
+  const long long g = wg % ngroups;
+  const int sg = (int)(wg / ngroups);
+  const long long row0 = g * ROWS;
+  const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
+  const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
+  const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
+  const E* in = static_cast<const E*>(a.in);
+  E* out = static_cast<E*>(a.out);
+
+  const coef5<T>* crow[V];
+  coef5<T> cinf[V];
+  T vyz[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const long long rr = row0 + lane + 32 * v;
+    const bool act = rr < nrows;
+    const int j = act ? (int)(rr % a.ny) : 0;
+    const int k = act ? (int)(rr / a.ny) : 0;
+    crow[v] = static_cast<const coef5<T>*>(a.coef) + (size_t)j * (lt + 1);
+    cinf[v] = crow[v][lt];
+    const T y = (T)(a.y0 + (double)j * a.hy), z = (T)(a.z0 + (double)k * a.hz);
+    vyz[v] = (T)a.hnu2 * y * y + (T)a.hlam2 * z * z;
+  }
+  const T s = (T)(*a.scale), hg2 = (T)a.hgam2, gg = (T)a.g, dt = (T)a.dt;
+  const T xs = (T)a.x0, hx = (T)a.hx;
+  // psi at position p of lane row v, scaled and advanced by H1
+  auto h1 = [&](E psi, int p, int v) -> E {
+    psi = s * psi;
+    const T x = xs + (T)p * hx;
+    const T en = hg2 * x * x + vyz[v] + gg * abs2(psi);
+    if (IMAG) {
+      return exp_t(-dt * en) * psi;
+    } else {
+      T sn, cs;
+      sincos_t(dt * en, &sn, &cs);
+      return psi * mk<T>(cs, -sn);
+    }
+  };
+  auto slot = [&](int q) { return ring + (size_t)(q % R) * SLOT; };
+  auto issue = [&](int q) {
+    if (q < qb) {
+      E* sl = slot(q);
+      for (int t = lane; t < ROWS * LPR; t += 32) {
+        const int row = t / LPR, col = t % LPR;
+        const int p = q * C + col * EP;
+        const long long rr = row0 + row;
+        E* dst = sl + row * PITCH + col * EP;
+        if (rr < nrows && p < N) {
+          cp_async<EP * sizeof(E)>(dst, in + rr * N + p);
+        } else {
+#pragma unroll
+          for (int e = 0; e < EP; ++e) dst[e] = zero<T>();
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // lane-row access to points 2k, 2k+1 through one 16-byte shared access
+  // (float) or two (double)
+  auto load2 = [&](const E* rp, int k, E& e0, E& e1) {
+    if (F32) {
+      const float4 t = reinterpret_cast<const float4*>(rp)[k];
+      e0 = mk<T>((T)t.x, (T)t.y);
+      e1 = mk<T>((T)t.z, (T)t.w);
+    } else {
+      e0 = rp[2 * k];
+      e1 = rp[2 * k + 1];
+    }
+  };
+  auto store2 = [&](E* rp, int k, E e0, E e1) {
+    if (F32) {
+      reinterpret_cast<float4*>(rp)[k] =
+          make_float4((float)e0.x, (float)e0.y, (float)e1.x, (float)e1.y);
+    } else {
+      rp[2 * k] = e0;
+      rp[2 * k + 1] = e1;
+    }
+  };
+  // forward sweep over one chunk of the lane's V rows (psi -> d' in place)
+  auto forward = [&](auto fast_tag, E* s0, int p0, E (&pm)[V], E (&d)[V]) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    E c0[V], c1[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      load2(s0 + (lane + 32 * v) * PITCH, 0, c0[v], c1[v]);
+      c0[v] = h1(c0[v], p0, v);
+      c1[v] = h1(c1[v], p0 + 1, v);
+    }
+#pragma unroll(unroll_of<C / 2>::value)
+    for (int k = 0; k < C / 2; ++k) {
+      const int p = p0 + 2 * k;
+      E n0[V], n1[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (k + 1 < C / 2) {
+          load2(s0 + (lane + 32 * v) * PITCH, k + 1, n0[v], n1[v]);
+          n0[v] = h1(n0[v], p + 2, v);
+          n1[v] = h1(n1[v], p + 3, v);
+        } else {
+          n0[v] = h1(s0[(lane + 32 * v) * PITCH + C], p + 2, v);
+          n1[v] = zero<T>();
+        }
+        d[v] = fwd(coef_at<T, FAST>(crow[v], cinf[v], p, lt), pm[v], c0[v], c1[v], d[v]);
+        const E e0 = d[v];
+        d[v] = fwd(coef_at<T, FAST>(crow[v], cinf[v], p + 1, lt), c0[v], c1[v], n0[v], d[v]);
+        store2(s0 + (lane + 32 * v) * PITCH, k, e0, d[v]);
+        pm[v] = c1[v];
+        c0[v] = n0[v];
+        c1[v] = n1[v];
+      }
+    }
+  };
+  // back substitution over chunk slot sp (positions p0..p0+C-1), x carried in
+  auto backward = [&](auto fast_tag, E* sp, int p0, E (&x)[V]) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+#pragma unroll(unroll_of<C / 2>::value)
+    for (int k = C / 2 - 1; k >= 0; --k) {
+      const int p = p0 + 2 * k;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        E d0, d1;
+        load2(sp + (lane + 32 * v) * PITCH, k, d0, d1);
+        if (FAST || p + 1 < N) x[v] = cfma(coef_at<T, FAST>(crow[v], cinf[v], p + 1, lt).be, x[v], d1);
+        const E e1 = x[v];
+        if (FAST || p < N) x[v] = cfma(coef_at<T, FAST>(crow[v], cinf[v], p, lt).be, x[v], d0);
+        store2(sp + (lane + 32 * v) * PITCH, k, x[v], e1);
+      }
+    }
+  };
+
+  for (int i = 0; i < R - 1; ++i) issue(qa + i);
+  E pm[V], d[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) pm[v] = d[v] = zero<T>();
+  for (int q = qa; q <= qb; ++q) {
+    if (q < qb) {
+      ring_wait(R);
+      __syncwarp();
+      if (q * C >= lt && (q + 1) * C <= N)
+        forward(bool_tag<true>{}, slot(q), q * C, pm, d);
+      else
+        forward(bool_tag<false>{}, slot(q), q * C, pm, d);
+    }
+    const int qq = q - 1;
+    if (qq >= qo0 && qq < qo1) {
+      E x[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) x[v] = zero<T>();
+      const int la = min(a.halo, N - q * C);
+      const E* sq = slot(q);
+      for (int h = la - 1; h >= 0; --h) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const E be = crow[v][min(q * C + h, lt)].be;
+          x[v] = cfma(be, x[v], sq[(lane + 32 * v) * PITCH + h]);
+        }
+      }
+      E* sp = slot(qq);
+      if (qq * C >= lt && q * C <= N)
+        backward(bool_tag<true>{}, sp, qq * C, x);
+      else
+        backward(bool_tag<false>{}, sp, qq * C, x);
+      __syncwarp();
+      // coalesced store of chunk qq
+#pragma unroll
+      for (int i = 0; i < ROWS * SPR / 32; ++i) {
+        const int t = i * 32 + lane;
+        const int row = t / SPR, col = t % SPR;
+        const int p = qq * C + col * EP;
+        const long long rr = row0 + row;
+        if (rr < nrows && p < N) {
+          const E* src = sp + row * PITCH + col * EP;
+          if (EP == 2)
+            *reinterpret_cast<float4*>(out + rr * N + p) = *reinterpret_cast<const float4*>(src);
+          else
+            out[rr * N + p] = *src;
+        }
+      }
+    }
+    __syncwarp();
+    issue(q + R - 1);
+  }
+  cp_async_wait<0>();
+}
+
+template <class T, int V, int C>
+static cudaError_t dispatch_x(bool imag, bool vec16, const stream_args& a, const sweep_shape& sh,
+                              cudaStream_t s) {
+  static bool done[4] = {false, false, false, false};
+  auto fn = vec16 ? (imag ? k_sweep_x<T, V, C, true, true> : k_sweep_x<T, V, C, false, true>)
+                  : (imag ? k_sweep_x<T, V, C, true, false> : k_sweep_x<T, V, C, false, false>);
+  cudaError_t e = allow_smem((const void*)fn, &done[(vec16 ? 2 : 0) + (imag ? 1 : 0)]);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Every (precision, V, C) combination the host can choose is instantiated
+// here; anything else is rejected before a launch.
+cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,
+                           cudaStream_t s) {
+  if (fp64) {
+    if (sh.V == 1 && sh.C == 16) return dispatch_x<double, 1, 16>(imag, true, a, sh, s);
+    if (sh.V == 1 && sh.C == 64) return dispatch_x<double, 1, 64>(imag, true, a, sh, s);
+    return cudaErrorInvalidValue;
+  }
+  if (sh.V == 2 && sh.C == 8) return dispatch_x<float, 2, 8>(imag, sh.vec16, a, sh, s);
+  if (sh.V == 2 && sh.C == 16) return dispatch_x<float, 2, 16>(imag, sh.vec16, a, sh, s);
+  if (sh.V == 1 && sh.C == 16) return dispatch_x<float, 1, 16>(imag, sh.vec16, a, sh, s);
+  if (sh.V == 1 && sh.C == 64) return dispatch_x<float, 1, 64>(imag, sh.vec16, a, sh, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace rotgp

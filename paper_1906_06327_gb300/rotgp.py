@@ -32,7 +32,7 @@ ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECU
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
            "rotgp_set_omega", "rotgp_init_analytic", "rotgp_set_psi", "rotgp_get_psi",
            "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
-           "rotgp_info", "rotgp_profile_enable", "rotgp_profile_read")
+           "rotgp_info", "rotgp_tune", "rotgp_profile_enable", "rotgp_profile_read")
 
 
 class Grid(ctypes.Structure):
@@ -59,8 +59,10 @@ class KStat(ctypes.Structure):
 
 
 class SolverInfo(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("halo", ctypes.c_int), ("chunk_x", ctypes.c_int),
-                ("chunk_s", ctypes.c_int), ("table_len", ctypes.c_int),
+    _fields_ = [("precision", ctypes.c_int), ("halo", ctypes.c_int), ("table_len", ctypes.c_int),
+                ("chunk", ctypes.c_int * 3), ("segments", ctypes.c_int * 3),
+                ("lines_per_lane", ctypes.c_int * 3), ("ring", ctypes.c_int * 3),
+                ("warps_per_block", ctypes.c_int * 3),
                 ("decay", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
 
 
@@ -107,6 +109,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
         lib.rotgp_sync.argtypes = [vp]
         lib.rotgp_info.argtypes = [vp, ctypes.POINTER(SolverInfo)]
+        lib.rotgp_tune.argtypes = [vp, ip, ip, ip, ip, ip, ip]
         lib.rotgp_profile_enable.argtypes = [vp, ip]
         lib.rotgp_profile_read.argtypes = [vp, ctypes.POINTER(KStat), ip, ctypes.POINTER(ip)]
         _lib = lib
@@ -224,7 +227,16 @@ class Solver:
     def info(self) -> dict:
         i = SolverInfo()
         self._check(self._lib.rotgp_info(self._h, ctypes.byref(i)))
-        return {k: getattr(i, k) for k, _ in SolverInfo._fields_}
+        out = {}
+        for k, _ in SolverInfo._fields_:
+            v = getattr(i, k)
+            out[k] = list(v)[:self.dim] if isinstance(v, ctypes.Array) else v
+        return out
+
+    def tune(self, axis: int, lines_per_lane: int, chunk: int, ring: int, warps_per_block: int,
+             segments: int):
+        self._check(self._lib.rotgp_tune(self._h, int(axis), int(lines_per_lane), int(chunk),
+                                         int(ring), int(warps_per_block), int(segments)))
 
     # -- timing
     def profile(self, on: bool = True):

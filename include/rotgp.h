@@ -121,8 +121,9 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision,
                  void* stream, rotgp_ctx** out);
 void rotgp_destroy(rotgp_ctx* ctx);
 
-/* Message of the last error on ctx (or of the last failed rotgp_create on
- * this thread when ctx is NULL).  Valid until the next call on ctx. */
+/* Message of the last error on ctx (or of the last failed rotgp_create or
+ * rotgp_observables_noalloc on this thread when ctx is NULL).  Valid until
+ * the next call on ctx. */
 const char* rotgp_last_error(const rotgp_ctx* ctx);
 
 /* Change the physics (all fields); rebuilds the per-line tables on the
@@ -180,6 +181,29 @@ int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring
  * and clears the accumulated records. */
 int rotgp_profile_enable(rotgp_ctx* ctx, int on);
 int rotgp_profile_read(rotgp_ctx* ctx, rotgp_kstat* out, int max, int* count);
+
+/* Observables of a wave function held in the caller's device memory, with
+ * no device-memory allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code whose device
+ * memory belongs to another allocator, code under a fixed memory budget
+ * reserved up front, and monitoring loops that must not add the device
+ * synchronisation cudaMalloc/cudaFree can bring.
+ *  grid, phys, precision  as for rotgp_create (dt is not used)
+ *  psi_device  device pointer to (N_x+1)(N_y+1)[(N_z+1)] complex points in
+ *              the ABI layout (complex double for ROTGP_FP64, complex float
+ *              for ROTGP_FP32); edge points are read as zero
+ *  stream      cudaStream_t to run on; the call synchronises it
+ *  out         host struct filled like rotgp_observables, except that step
+ *              is 0 and vortices is -1 (not evaluated)
+ * Scratch: a file-scope device array of 416 KiB inside the library, which
+ * every GPU that loads the library holds until exit.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race and must
+ * be ordered by the caller.  At most 33,554,432 grid points; larger grids
+ * are rejected with ROTGP_EINVAL (message via rotgp_last_error(NULL)). */
+int rotgp_observables_noalloc(const rotgp_grid* grid, const rotgp_phys* phys, int precision,
+                              const void* psi_device, void* stream, rotgp_obs* out);
 
 #ifdef __cplusplus
 }

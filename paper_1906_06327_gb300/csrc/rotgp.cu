@@ -422,6 +422,11 @@ int dev_alloc(rotgp_ctx* c, void** p, size_t bytes) {
 
 }  // namespace
 
+namespace rotgp {
+// Message returned by rotgp_last_error(NULL) on this thread.
+void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace rotgp
+
 // =============================================================== C ABI
 extern "C" {
 

@@ -32,7 +32,8 @@ ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECU
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
            "rotgp_set_omega", "rotgp_init_analytic", "rotgp_set_psi", "rotgp_get_psi",
            "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
-           "rotgp_info", "rotgp_tune", "rotgp_profile_enable", "rotgp_profile_read")
+           "rotgp_info", "rotgp_tune", "rotgp_profile_enable", "rotgp_profile_read",
+           "rotgp_observables_noalloc")
 
 
 class Grid(ctypes.Structure):
@@ -112,6 +113,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_tune.argtypes = [vp, ip, ip, ip, ip, ip, ip]
         lib.rotgp_profile_enable.argtypes = [vp, ip]
         lib.rotgp_profile_read.argtypes = [vp, ctypes.POINTER(KStat), ip, ctypes.POINTER(ip)]
+        lib.rotgp_observables_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Phys), ip,
+                                                  vp, vp, ctypes.POINTER(Obs)]
         _lib = lib
         return lib
 
@@ -249,6 +252,28 @@ class Solver:
         return {r.name.decode(): {"launches": r.launches, "total_ms": r.total_ms,
                                   "bytes_per_launch": r.bytes_per_launch}
                 for r in recs[:cnt.value]}
+
+
+def observables_noalloc(n, h, psi, *, gamma=1.0, nu=1.0, lam=1.0, g=0.0, omega=0.0,
+                        stream=0) -> dict:
+    """Observables of a CUDA tensor holding an ABI-layout wave function,
+    through rotgp_observables_noalloc (no device allocation; see rotgp.h)."""
+    lib = load()
+    n, h = tuple(int(v) for v in n), tuple(float(v) for v in h)
+    dim = len(n)
+    ptr, on_dev, is64, _keep = _buffer(psi, _shape(n))
+    if not on_dev:
+        raise ValueError("psi must be in device memory")
+    grid = Grid(dim, (ctypes.c_int * 3)(*(list(n) + [0] * (3 - dim))),
+                (ctypes.c_double * 3)(*(list(h) + [0.0] * (3 - dim))))
+    phys = Phys(gamma, nu, lam, g, omega, 1.0)
+    o = Obs()
+    rc = lib.rotgp_observables_noalloc(ctypes.byref(grid), ctypes.byref(phys),
+                                       ROTGP_FP64 if is64 else ROTGP_FP32, ctypes.c_void_p(ptr),
+                                       ctypes.c_void_p(int(stream)), ctypes.byref(o))
+    if rc != ROTGP_OK:
+        raise RotgpError(rc, lib.rotgp_last_error(None).decode())
+    return o.as_dict()
 
 
 def _buffer(obj, shape):

@@ -107,6 +107,8 @@ typedef struct {
   int segments[3];        /* independent segments each line is split into */
   int lines_per_lane[3];  /* lines one GPU thread solves together         */
   int ring[3];            /* chunk slots in flight per warp               */
+  int stencil_taps[3];    /* taps of the banded-inverse stencil in use,
+                             0 when the axis uses the Thomas solve        */
   int warps_per_block[3];
   double decay;           /* largest per-point decay of a truncated carry */
   size_t device_bytes;    /* device memory owned by the context           */
@@ -174,6 +176,20 @@ int rotgp_info(const rotgp_ctx* ctx, rotgp_solver_info* out);
  * autotuner.  ROTGP_EINVAL for a shape that is not built or does not fit. */
 int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring,
                int warps_per_block, int segments);
+
+/* Line solver of one sweep (axis 0 = x, 1 = y, 2 = z).
+ * ROTGP_SOLVER_THOMAS: the Thomas algorithm on each line (chunked, with the
+ *   truncated-carry halo of rotgp_info); every precision.
+ * ROTGP_SOLVER_STENCIL: the same CN substep as psi' = (2 A^{-1} - I) psi
+ *   with W = 2 A^{-1} - I applied as a banded stencil (its entries decay
+ *   geometrically away from the diagonal; the dropped tail is below 2e-10
+ *   of the largest weight and the end rows of each line are exact).
+ *   Complex float only, and only where rotgp_info reports stencil taps at
+ *   create time (ROTGP_EUNSUPPORTED otherwise).  The default wherever it
+ *   is available. */
+#define ROTGP_SOLVER_THOMAS 0
+#define ROTGP_SOLVER_STENCIL 1
+int rotgp_set_solver(rotgp_ctx* ctx, int axis, int solver);
 
 /* Per-kernel CUDA-event timing.  While enabled, every kernel launch of the
  * context is bracketed by events on its stream.  rotgp_profile_read

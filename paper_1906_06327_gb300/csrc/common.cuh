@@ -82,6 +82,11 @@ struct stream_args {
   double dt, g, hgam2, hnu2, hlam2;
   double x0, hx, y0, hy, z0, hz;
   const double* scale;  // pending renormalisation applied as the state is read
+  // banded-inverse stencil sweeps (complex float): weights [line][2B+1][2K+1]
+  const void* wtab;
+  int taps_k;         // K: taps reach K points either side
+  int brows;          // B: rows with their own weights at each line end
+  int tile_rows;      // x stencil: row pairs per warp task
   // norm reduction in the last sweep of a step
   double vol;
   int imag;
@@ -98,6 +103,7 @@ struct obs_args {
   double hx, hy, hz, x0, y0, z0;
   double hgam2, hnu2, hlam2, g, omega;
   const double* scale;
+  int rows_per_block;  // x rows (j, k) reduced by one block
   double* partials;
   unsigned int* counter;
   double* result;  // NOBS doubles
@@ -135,6 +141,15 @@ cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const swe
 cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
                                  const sweep_shape& sh, cudaStream_t s);
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);
+// banded-inverse stencil form of the complex-float sweeps (stencil.cu)
+cudaError_t launch_stencil_tables(void* wtab, int nlines, int K, int B, int m,
+                                  const axis_coef& co, cudaStream_t s);
+cudaError_t launch_stencil_x(bool imag, const stream_args& a, long long warps, cudaStream_t s);
+cudaError_t launch_stencil_strided(bool reduce, const stream_args& a, long long warps,
+                                   int wpb, cudaStream_t s);
+inline bool stencil_k_built(int K) { return K == 4 || K == 6 || K == 8; }
+// blocks of the strided stencil launch (tasks of 64 columns x 16 points)
+long long stencil_strided_blocks(long long nlines, int len, int wpb);
 // Is (precision, V, C) one of the instantiated sweep kernels?
 inline bool sweep_shape_built(bool fp64, int V, int C) {
   if (fp64) return V == 1 && (C == 16 || C == 64);

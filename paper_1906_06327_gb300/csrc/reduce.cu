@@ -77,54 +77,69 @@ template <class T>
 __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
   using C = cpx<T>;
   const C* psi = static_cast<const C*>(a.psi);
-  const long long nx = a.nx, ny = a.ny, nz = a.nz;
-  const long long sites = nx * ny * nz;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const long long plane = (long long)nx * ny;
   const T s = (T)(*a.scale);
   const T ihx2 = (T)(1.0 / (a.hx * a.hx)), ihy2 = (T)(1.0 / (a.hy * a.hy));
   const T ihz2 = a.dim == 3 ? (T)(1.0 / (a.hz * a.hz)) : (T)0;
   const T i2hx = (T)(0.5 / a.hx), i2hy = (T)(0.5 / a.hy);
   const T om = (T)a.omega, g = (T)a.g;
+  // per-thread sums over a short strip of sites in the working precision,
+  // promoted to double for the block and grid reduction
+  T t[NQ];
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) t[v] = 0;
+  const int nrows = ny * nz;
+  const int r0 = blockIdx.x * a.rows_per_block, r1 = min(nrows, r0 + a.rows_per_block);
+  for (int row = r0; row < r1; ++row) {
+    const int j = row % ny, k = row / ny;
+    if (j == 0 || (a.dim == 3 && k == 0)) continue;
+    const T y = (T)(a.y0 + (double)j * a.hy);
+    const T z = a.dim == 3 ? (T)(a.z0 + (double)k * a.hz) : (T)0;
+    const T vyz = (T)a.hnu2 * y * y + (T)a.hlam2 * z * z;
+    const C* rp = psi + (long long)row * nx;
+    const bool has_yp = j + 1 < ny, has_zp = a.dim == 3 && k + 1 < nz;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      if (i == 0) continue;
+      const T x = (T)(a.x0 + (double)i * a.hx);
+      const T V = (T)a.hgam2 * x * x + vyz;
+      const C c = s * rp[i];
+      const C xp = i + 1 < nx ? s * rp[i + 1] : mk<T>(0, 0);
+      const C xm = s * rp[i - 1];
+      const C yp = has_yp ? s * rp[i + nx] : mk<T>(0, 0);
+      const C ym = s * rp[i - nx];
+      C lap = ihx2 * (xp + xm - (T)2 * c) + ihy2 * (yp + ym - (T)2 * c);
+      if (a.dim == 3) {
+        const C zp = has_zp ? s * rp[i + plane] : mk<T>(0, 0);
+        const C zm = s * rp[i - plane];
+        lap = lap + ihz2 * (zp + zm - (T)2 * c);
+      }
+      const C dx = i2hx * (xp - xm), dy = i2hy * (yp - ym);
+      const T re = c.x, im = c.y, dens = re * re + im * im;
+      const T hr = (T)-0.5 * lap.x + V * re + om * (y * dx.y - x * dy.y);
+      const T hi = (T)-0.5 * lap.y + V * im + om * (-(y * dx.x) + x * dy.x);
+      // -Omega L_z psi = -Omega i (y D_x - x D_y) psi
+      const C lz = y * dx - x * dy;  // L_z psi / i
+      const C hlin = mk<T>((T)-0.5 * lap.x + V * c.x + om * lz.y,
+                           (T)-0.5 * lap.y + V * c.y - om * lz.x);
+      t[0] += dens;
+      t[1] += re * re;
+      t[2] += im * im;
+      t[3] += re * hr;
+      t[4] += g * dens * re * re;
+      t[5] += im * hi;
+      t[6] += g * dens * im * im;
+      t[7] += re * hlin.x + im * hlin.y;
+      t[8] += g * dens * dens;
+      t[9] += x * x * dens;
+      t[10] += y * y * dens;
+      t[11] += z * z * dens;
+      t[12] = t[12] > dens ? t[12] : dens;
+    }
+  }
   double q[NQ];
 #pragma unroll
-  for (int v = 0; v < NQ; ++v) q[v] = 0.0;
-  auto at = [&](long long i, long long j, long long k) -> C {
-    if (i >= nx || j >= ny || k >= nz) return mk<T>(0, 0);  // implicit edge N
-    return s * psi[(k * ny + j) * nx + i];
-  };
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < sites;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long i = idx % nx, j = (idx / nx) % ny, k = idx / (nx * ny);
-    if (i == 0 || j == 0 || (a.dim == 3 && k == 0)) continue;
-    const T x = (T)(a.x0 + (double)i * a.hx), y = (T)(a.y0 + (double)j * a.hy);
-    const T z = a.dim == 3 ? (T)(a.z0 + (double)k * a.hz) : (T)0;
-    const T V = (T)a.hgam2 * x * x + (T)a.hnu2 * y * y + (T)a.hlam2 * z * z;
-    const C c = s * psi[idx];
-    const C xp = at(i + 1, j, k), xm = at(i - 1, j, k);
-    const C yp = at(i, j + 1, k), ym = at(i, j - 1, k);
-    C lap = ihx2 * (xp + xm - (T)2 * c) + ihy2 * (yp + ym - (T)2 * c);
-    if (a.dim == 3) lap = lap + ihz2 * (at(i, j, k + 1) + at(i, j, k - 1) - (T)2 * c);
-    const C dx = i2hx * (xp - xm), dy = i2hy * (yp - ym);
-    const T re = c.x, im = c.y, dens = re * re + im * im;
-    const T hr = (T)-0.5 * lap.x + V * re + om * (y * dx.y - x * dy.y);
-    const T hi = (T)-0.5 * lap.y + V * im + om * (-(y * dx.x) + x * dy.x);
-    // -Omega L_z psi = -Omega i (y D_x - x D_y) psi
-    const C lz = y * dx - x * dy;  // L_z psi / i
-    const C hlin = mk<T>((T)-0.5 * lap.x + V * c.x + om * lz.y,
-                         (T)-0.5 * lap.y + V * c.y - om * lz.x);
-    q[0] += (double)dens;
-    q[1] += (double)(re * re);
-    q[2] += (double)(im * im);
-    q[3] += (double)(re * hr);
-    q[4] += (double)(g * dens * re * re);
-    q[5] += (double)(im * hi);
-    q[6] += (double)(g * dens * im * im);
-    q[7] += (double)(re * hlin.x + im * hlin.y);
-    q[8] += (double)(g * dens * dens);
-    q[9] += (double)(x * x * dens);
-    q[10] += (double)(y * y * dens);
-    q[11] += (double)(z * z * dens);
-    q[12] = fmax(q[12], (double)dens);
-  }
+  for (int v = 0; v < NQ; ++v) q[v] = (double)t[v];
   if (!block_partials<NQ, true>(q, a.partials, a.counter)) return;
   __shared__ double fin[NQ];
   __threadfence();

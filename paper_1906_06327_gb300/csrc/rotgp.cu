@@ -40,6 +40,11 @@ struct AxisPlan {
   int len = 0;          // points per line
   int nseg = 1, seg_chunks = 1, warm = 1;
   sweep_shape sh{};
+  // banded-inverse stencil (complex float): taps K, end rows B, weights [mode]
+  bool stencil_ok = false;  // stencil form available for this axis
+  bool use_stencil = false;
+  int sK = 0, sB = 0, snseg = 1, swpb = 1;
+  void* wtab[2] = {nullptr, nullptr};
 };
 
 struct ProfRec {
@@ -194,6 +199,78 @@ int plan_solver(rotgp_ctx* c, int* halo, int* lt, double* decay) {
   return ROTGP_OK;
 }
 
+// Rows of W = 2 A^{-1} - I for a short line of m unknowns with the
+// coefficients of line u of an axis (double, Thomas solves column by
+// column): W[p][j] for p, j = 1..m, stored row-major in w (size (m+1)^2).
+void short_line_w(const axis_coef& co, double u, int m, std::vector<cd>& w) {
+  const cd kap(co.kap_re, co.kap_im), tau = cd(co.tau_re, co.tau_im) * u;
+  const cd a0 = 1.0 + 2.0 * kap, am = -kap + tau, ap = -kap - tau;
+  std::vector<cd> c(m + 2), mm(m + 2), d(m + 2);
+  c[0] = 0.0;
+  for (int i = 1; i <= m; ++i) {
+    mm[i] = 1.0 / (a0 - am * c[i - 1]);
+    c[i] = ap * mm[i];
+  }
+  w.assign((size_t)(m + 1) * (m + 1), 0.0);
+  for (int j = 1; j <= m; ++j) {
+    d[0] = 0.0;
+    for (int i = 1; i <= m; ++i) d[i] = ((i == j ? 1.0 : 0.0) - am * d[i - 1]) * mm[i];
+    for (int i = m - 1; i >= 1; --i) d[i] = d[i] - c[i] * d[i + 1];
+    for (int i = 1; i <= m; ++i) w[(size_t)i * (m + 1) + j] = 2.0 * d[i] - (i == j ? 1.0 : 0.0);
+  }
+}
+
+// Stencil size of one axis (both modes, worst line): the smallest K in
+// {4, 6, 8} whose dropped taps are below 2e-10 of the largest weight, and
+// the number B of rows at each line end that differ from the interior row
+// by more than 1e-10 of it.  Returns false when no built K is enough.
+bool plan_stencil(rotgp_ctx* c, int a, int* K_out, int* B_out) {
+  const int N = a == 0 ? c->nx : (a == 1 ? c->ny : c->nz);
+  const int nl = a == 0 ? c->ny : (a == 1 ? c->nx : 1);
+  const int m = 84;  // short line: interior row at 42, far from both ends
+  int K = 0, B = 0;
+  std::vector<cd> w;
+  for (int mode = 0; mode < 2; ++mode) {
+    const axis_coef co = make_coef(a, mode, c->grid.h[a], c->phys.dt, c->phys.omega,
+                                   nlines_u0(c, a), nlines_du(c, a));
+    for (int l : {0, nl - 1, nl / 2}) {
+      short_line_w(co, co.u0 + l * co.du, m, w);
+      auto W = [&](int i, int j) { return w[(size_t)i * (m + 1) + j]; };
+      const int mid = m / 2;
+      const double w0 = std::abs(W(mid, mid));
+      int k = 0;
+      for (int kk : {4, 6, 8}) {
+        if (std::abs(W(mid, mid - kk - 1)) <= 2e-10 * w0 && std::abs(W(mid, mid + kk + 1)) <= 2e-10 * w0) {
+          k = kk;
+          break;
+        }
+      }
+      if (!k) return false;
+      K = std::max(K, k);
+      // first row from each end that equals the interior row within 1e-10
+      for (int e = 1; e < mid - 8; ++e) {
+        double dl = 0, dr = 0;
+        for (int t = -8; t <= 8; ++t) {
+          const cd ref = W(mid, mid + t);
+          if (e + t >= 1) dl = std::max(dl, std::abs(W(e, e + t) - ref));
+          if (m + 1 - e + t <= m && m + 1 - e + t >= 1)
+            dr = std::max(dr, std::abs(W(m + 1 - e, m + 1 - e + t) - ref));
+        }
+        if (dl <= 1e-10 * w0 && dr <= 1e-10 * w0) {
+          B = std::max(B, e);
+          break;
+        }
+        if (e == mid - 9) return false;
+      }
+    }
+  }
+  B = std::max(B, K + 1);
+  if (N < 2 * B + 2) return false;
+  *K_out = K;
+  *B_out = B;
+  return true;
+}
+
 // Set the launch shape of axis a: V lines per lane, chunk C, R ring slots,
 // wpb warps per block, nseg segments per line; recompute blocks and shared
 // memory.  Only shapes with an instantiated kernel are accepted.
@@ -251,6 +328,26 @@ int plan_axes(rotgp_ctx* c) {
     const long long groups = (ap.lines + 32 * V - 1) / (32 * V);
     int rc = set_shape(c, a, V, C, R, 1, std::max<long long>(1, target / groups));
     if (rc) return rc == ROTGP_EINVAL ? fail(c, ROTGP_EUNSUPPORTED, "%s", c->err.c_str()) : rc;
+    // banded-inverse stencil: complex float, even N_x (two columns per lane),
+    // x lines a multiple of 4 points
+    int K = 0, B = 0;
+    const bool sized = ap.wtab[0] != nullptr;  // tables already allocated
+    ap.stencil_ok = !c->fp64 && c->nx % 2 == 0 && (!x || ap.len % 4 == 0) &&
+                    plan_stencil(c, a, &K, &B);
+    if (sized) {
+      // keep the allocated size; a larger K or B than needed is only more exact
+      ap.stencil_ok = ap.stencil_ok && K <= ap.sK && B <= ap.sB;
+      ap.use_stencil = ap.use_stencil && ap.stencil_ok;
+      continue;
+    }
+    if (ap.stencil_ok) {
+      ap.sK = K;
+      ap.sB = B;
+      // strided stencil: independent tasks of 64 columns x 16 points
+      ap.swpb = 4;
+      ap.snseg = 1;
+    }
+    ap.use_stencil = ap.stencil_ok;
   }
   return ROTGP_OK;
 }
@@ -301,6 +398,9 @@ int build_tables(rotgp_ctx* c) {
       Timed t(c, K_TABLES);
       cudaError_t e = launch_tables(c->fp64, ap.table[mode], ap.nlines, c->lt, ap.co[mode],
                                     c->stream);
+      if (e == cudaSuccess && ap.stencil_ok && ap.wtab[mode])
+        e = launch_stencil_tables(ap.wtab[mode], ap.nlines, ap.sK, ap.sB,
+                                  2 * ap.sB + 2 * ap.sK + 8, ap.co[mode], c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "table kernel");
     }
   }
@@ -332,6 +432,9 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
   a.scale_out = c->d_scale();
   a.norm_out = c->d_norm();
   a.flags = c->d_flags();
+  a.wtab = ap.wtab[mode];
+  a.taps_k = ap.sK;
+  a.brows = ap.sB;
   cudaError_t e;
   if (axis == 0) {
     a.coef_mode = 2;
@@ -348,13 +451,23 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
     a.scale = c->d_scale();
     Timed t(c, K_SWEEP_X);
-    e = launch_sweep_x(c->fp64, imag, a, ap.sh, c->stream);
+    if (ap.use_stencil) {
+      const long long warps = ((ap.lines + 1) / 2) * ((ap.len + 127) / 128);
+      e = launch_stencil_x(imag, a, warps, c->stream);
+    } else {
+      e = launch_sweep_x(c->fp64, imag, a, ap.sh, c->stream);
+    }
   } else {
     a.stride = axis == 1 ? (long long)c->nx : (long long)c->nx * c->ny;
     a.outer = axis == 1 ? (long long)c->nx * c->ny : (long long)c->nx;
     a.coef_mode = axis == 1 ? 1 : 0;
     Timed t(c, axis == 1 ? K_SWEEP_Y : K_SWEEP_Z);
-    e = launch_sweep_strided(c->fp64, last, a, ap.sh, c->stream);
+    if (ap.use_stencil) {
+      a.nseg = ap.snseg;
+      e = launch_stencil_strided(last, a, 0, ap.swpb, c->stream);
+    } else {
+      e = launch_sweep_strided(c->fp64, last, a, ap.sh, c->stream);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
   c->cur = 1 - c->cur;
@@ -396,8 +509,10 @@ void release(rotgp_ctx* c) {
   for (void*& p : c->psi) cudaFree(p), p = nullptr;
   cudaFree(c->staging);
   cudaFree(c->dR);
-  for (auto& ap : c->axis)
+  for (auto& ap : c->axis) {
     for (void*& t : ap.table) cudaFree(t), t = nullptr;
+    for (void*& t : ap.wtab) cudaFree(t), t = nullptr;
+  }
   cudaFree(c->partials);
   cudaFree(c->counter);
   cudaFree(c->scalars);
@@ -509,6 +624,19 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
   for (int a = 0; a < grid->dim && !rc; ++a)
     for (int m = 0; m < 2 && !rc; ++m)
       rc = dev_alloc(c, &c->axis[a].table[m], (size_t)c->axis[a].nlines * (c->lt + 1) * tab_elem);
+  for (int a = 0; a < grid->dim && !rc; ++a) {
+    AxisPlan& ap = c->axis[a];
+    if (!ap.stencil_ok) continue;
+    const size_t bytes = (size_t)ap.nlines * (2 * ap.sB + 1) * (2 * ap.sK + 1) * sizeof(cpx<float>);
+    for (int m = 0; m < 2 && !rc; ++m) rc = dev_alloc(c, &ap.wtab[m], bytes);
+  }
+  if (!rc) {
+    // the stencil form of the last sweep reduces the norm in its own blocks
+    const AxisPlan& last = c->axis[grid->dim - 1];
+    if (last.stencil_ok)
+      c->partial_doubles = std::max(
+          c->partial_doubles, (size_t)stencil_strided_blocks(last.lines, last.len, 1));
+  }
   if (!rc) rc = dev_alloc(c, (void**)&c->partials, c->partial_doubles * sizeof(double));
   if (!rc) rc = dev_alloc(c, (void**)&c->counter, sizeof(unsigned));
   if (!rc) rc = dev_alloc(c, (void**)&c->scalars, (2 + NOBS + 2) * sizeof(double));
@@ -577,6 +705,18 @@ int rotgp_set_phys(rotgp_ctx* c, const rotgp_phys* phys) {
   if (rc) {
     c->phys = old;
     return rc;
+  }
+  if (halo <= c->halo) {
+    // re-check the stencil sizes against the new physics (plan_axes keeps
+    // the allocated K and B and falls back to the Thomas form if they are
+    // no longer enough)
+    const int keep_h = c->halo;
+    rc = plan_axes(c);
+    c->halo = keep_h;
+    if (rc) {
+      c->phys = old;
+      return rc;
+    }
   }
   c->decay = std::max(c->decay, dec);
   return build_tables(c);
@@ -694,8 +834,13 @@ int rotgp_observables(rotgp_ctx* c, rotgp_obs* out) {
   a.result = c->d_obs();
   cudaError_t e;
   {
+    // about reduce_blocks() blocks, each over whole x rows
+    const long long nrows = (long long)c->ny * c->nz;
+    const long long want = reduce_blocks(c, c->sites);
+    a.rows_per_block = (int)((nrows + want - 1) / want);
+    const int blocks = (int)((nrows + a.rows_per_block - 1) / a.rows_per_block);
     Timed t(c, K_OBS);
-    e = launch_observables(c->fp64, a, reduce_blocks(c, c->sites), 256, c->stream);
+    e = launch_observables(c->fp64, a, blocks, 256, c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "observables kernel");
   vort_args v{};
@@ -765,6 +910,7 @@ int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
     out->segments[a] = on ? c->axis[a].nseg : 0;
     out->lines_per_lane[a] = on ? c->axis[a].sh.V : 0;
     out->ring[a] = on ? c->axis[a].sh.R : 0;
+    out->stencil_taps[a] = on && c->axis[a].use_stencil ? 2 * c->axis[a].sK + 1 : 0;
     out->warps_per_block[a] = on ? c->axis[a].sh.warps_per_block : 0;
   }
   out->table_len = c->lt;
@@ -782,8 +928,26 @@ int rotgp_tune(rotgp_ctx* c, int axis, int lines_per_lane, int chunk, int ring,
   if (segments < 1) return fail(c, ROTGP_EINVAL, "segments must be >= 1");
   const AxisPlan keep = c->axis[axis];
   int rc = set_shape(c, axis, lines_per_lane, chunk, ring, warps_per_block, segments);
-  if (rc) c->axis[axis] = keep;
-  return rc;
+  if (rc) {
+    c->axis[axis] = keep;
+    return rc;
+  }
+  AxisPlan& ap = c->axis[axis];
+  ap.snseg = std::max(1, std::min(segments, std::max(1, ap.len / 16)));
+  ap.swpb = std::min(warps_per_block, 4);
+  return ROTGP_OK;
+}
+
+int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
+  if (!c) return ROTGP_EINVAL;
+  if (axis < 0 || axis >= c->grid.dim) return fail(c, ROTGP_EINVAL, "axis out of range");
+  if (solver != ROTGP_SOLVER_THOMAS && solver != ROTGP_SOLVER_STENCIL)
+    return fail(c, ROTGP_EINVAL, "unknown solver %d", solver);
+  AxisPlan& ap = c->axis[axis];
+  if (solver == ROTGP_SOLVER_STENCIL && !ap.stencil_ok)
+    return fail(c, ROTGP_EUNSUPPORTED, "no stencil form for axis %d of this context", axis);
+  ap.use_stencil = solver == ROTGP_SOLVER_STENCIL;
+  return ROTGP_OK;
 }
 
 int rotgp_profile_enable(rotgp_ctx* c, int on) {

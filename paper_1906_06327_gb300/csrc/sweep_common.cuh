@@ -109,4 +109,150 @@ struct __align__(V * sizeof(cpx<T>)) pack {
   cpx<T> v[V];
 };
 
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-thread sum of |x|^2: Kahan-compensated in float, plain in double.
+template <class T>
+struct acc_t {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T v) {
+    T y = v - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <>
+struct acc_t<double> {
+  double s = 0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// Block sum of v -> per-block partial; the last block to finish sums the
+// partials in block order (deterministic), sets the norm, the pending scale
+// (1/sqrt(norm) in imaginary time, 1 in real time) and the non-finite flag.
+static __device__ void norm_epilogue(double v, const stream_args& a) {
+  __shared__ double ws[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned nblocks = gridDim.x;
+  v = warp_sum(v);
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += ws[w];
+    a.partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned t = atomicAdd(a.counter, 1u);
+    last = (t == nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0;
+  for (unsigned i = threadIdx.x; i < nblocks; i += blockDim.x) s += __ldcg(&a.partials[i]);
+  s = warp_sum(s);
+  __syncthreads();
+  if (lane == 0) ws[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0;
+    for (int w = 0; w < nw; ++w) tot += ws[w];
+    double n = tot * a.vol;
+    *a.norm_out = n;
+    if (!(n > 0.0) || !isfinite(n)) {
+      atomicOr(a.flags, 1);
+      *a.scale_out = 1.0;
+    } else {
+      *a.scale_out = a.imag ? 1.0 / sqrt(n) : 1.0;
+    }
+    *a.counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- packed FP32x2
+// Two lines solved by one lane in complex float are held in split form: the
+// real parts of both lines in one float2 and the imaginary parts in another,
+// so that every complex multiply-add of the two lines is four packed FP32x2
+// FMAs (__ffma2_rn) instead of eight scalar ones.
+struct c2 {
+  float2 re, im;
+};
+// a complex coefficient of the two lines, split, with negated imaginary parts
+struct k2 {
+  float2 x, y, ny;
+};
+struct coef2 {
+  k2 a0, am, ap, al, be;
+};
+
+__device__ __forceinline__ k2 make_k2(cpx<float> a, cpx<float> b) {
+  k2 k;
+  k.x = make_float2(a.x, b.x);
+  k.y = make_float2(a.y, b.y);
+  k.ny = make_float2(-a.y, -b.y);
+  return k;
+}
+__device__ __forceinline__ coef2 make_coef2(const coef5<float>& u, const coef5<float>& v) {
+  coef2 c;
+  c.a0 = make_k2(u.a0, v.a0);
+  c.am = make_k2(u.am, v.am);
+  c.ap = make_k2(u.ap, v.ap);
+  c.al = make_k2(u.al, v.al);
+  c.be = make_k2(u.be, v.be);
+  return c;
+}
+// k * b
+__device__ __forceinline__ c2 kmul2(const k2& k, const c2& b) {
+  c2 r;
+  r.re = __ffma2_rn(k.ny, b.im, __fmul2_rn(k.x, b.re));
+  r.im = __ffma2_rn(k.y, b.re, __fmul2_rn(k.x, b.im));
+  return r;
+}
+// k * b + c
+__device__ __forceinline__ c2 kfma2(const k2& k, const c2& b, const c2& c) {
+  c2 r;
+  r.re = __ffma2_rn(k.ny, b.im, __ffma2_rn(k.x, b.re, c.re));
+  r.im = __ffma2_rn(k.y, b.re, __ffma2_rn(k.x, b.im, c.im));
+  return r;
+}
+// forward step of both lines: d' = a0 pc + am pm + ap pn + al d'
+__device__ __forceinline__ c2 fwd2(const coef2& k, const c2& pm, const c2& pc, const c2& pn,
+                                   const c2& d) {
+  return kfma2(k.al, d, kfma2(k.ap, pn, kfma2(k.am, pm, kmul2(k.a0, pc))));
+}
+__device__ __forceinline__ c2 zero2() {
+  c2 r;
+  r.re = make_float2(0.f, 0.f);
+  r.im = make_float2(0.f, 0.f);
+  return r;
+}
+// two interleaved complex numbers (line 0, line 1) <-> split form
+__device__ __forceinline__ c2 split2(const float4& t) {
+  c2 r;
+  r.re = make_float2(t.x, t.z);
+  r.im = make_float2(t.y, t.w);
+  return r;
+}
+__device__ __forceinline__ float4 join2(const c2& c) {
+  return make_float4(c.re.x, c.im.x, c.re.y, c.im.y);
+}
+// split form stored as one float4 (re0, re1, im0, im1)
+__device__ __forceinline__ float4 pack_split(const c2& c) {
+  return make_float4(c.re.x, c.re.y, c.im.x, c.im.y);
+}
+__device__ __forceinline__ c2 unpack_split(const float4& t) {
+  c2 r;
+  r.re = make_float2(t.x, t.y);
+  r.im = make_float2(t.z, t.w);
+  return r;
+}
+
 }  // namespace rotgp

@@ -12,74 +12,6 @@
 
 namespace rotgp {
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Per-thread sum of |x|^2: Kahan-compensated in float, plain in double.
-template <class T>
-struct acc_t {
-  T s = 0, c = 0;
-  __device__ __forceinline__ void add(T v) {
-    T y = v - c;
-    T t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-template <>
-struct acc_t<double> {
-  double s = 0;
-  __device__ __forceinline__ void add(double v) { s += v; }
-  __device__ __forceinline__ double value() const { return s; }
-};
-
-// Block sum of v -> per-block partial; the last block to finish sums the
-// partials in block order (deterministic), sets the norm, the pending scale
-// (1/sqrt(norm) in imaginary time, 1 in real time) and the non-finite flag.
-__device__ void norm_epilogue(double v, const stream_args& a) {
-  __shared__ double ws[32];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const unsigned nblocks = gridDim.x;
-  v = warp_sum(v);
-  if (lane == 0) ws[warp] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0;
-    for (int w = 0; w < nw; ++w) s += ws[w];
-    a.partials[blockIdx.x] = s;
-    __threadfence();
-    unsigned t = atomicAdd(a.counter, 1u);
-    last = (t == nblocks - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double s = 0;
-  for (unsigned i = threadIdx.x; i < nblocks; i += blockDim.x) s += __ldcg(&a.partials[i]);
-  s = warp_sum(s);
-  __syncthreads();
-  if (lane == 0) ws[warp] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0;
-    for (int w = 0; w < nw; ++w) tot += ws[w];
-    double n = tot * a.vol;
-    *a.norm_out = n;
-    if (!(n > 0.0) || !isfinite(n)) {
-      atomicOr(a.flags, 1);
-      *a.scale_out = 1.0;
-    } else {
-      *a.scale_out = a.imag ? 1.0 / sqrt(n) : 1.0;
-    }
-    *a.counter = 0u;
-  }
-}
-
 // --------------------------------------------------------------- tables
 // Thomas multipliers of one line, m_1 = 1/A0, c'_1 = A+ m_1,
 // m_p = 1/(A0 - A- c'_{p-1}), c'_p = A+ m_p, folded into coef5 entries
@@ -259,6 +191,149 @@ __global__ void __launch_bounds__(128) k_sweep_strided(const stream_args a) {
   if (REDUCE) norm_epilogue(acc.value(), a);
 }
 
+// Complex float, two lines per lane: the same pipeline with the two lines in
+// split form (packed FP32x2 arithmetic, sweep_common.cuh); d' is kept in the
+// ring in split form and joined back to interleaved complex on the store.
+template <int C, bool FAST>
+__device__ __forceinline__ void strided_forward2(float4* s0, c2& pm, c2& d,
+                                                 const coef5<float>* const (&crow)[2],
+                                                 const coef2& cf, int p0, int lt) {
+  // stage the chunk (and the next point) in registers first: the solve then
+  // never waits on a shared load queued behind its own stores
+  float4 w[C + 1];
+#pragma unroll
+  for (int r = 0; r <= C; ++r) w[r] = s0[r * 32];
+  c2 cur = split2(w[0]);
+#pragma unroll
+  for (int r = 0; r < C; ++r) {
+    const c2 nx = split2(w[r + 1]);
+    coef2 k;
+    if (FAST) {
+      k = cf;
+    } else {
+      const int i = min(p0 + r, lt);
+      k = make_coef2(crow[0][i], crow[1][i]);
+    }
+    d = fwd2(k, pm, cur, nx, d);
+    pm = cur;
+    w[r] = pack_split(d);
+    cur = nx;
+  }
+#pragma unroll
+  for (int r = 0; r < C; ++r) s0[r * 32] = w[r];
+}
+
+template <int C, bool REDUCE>
+__global__ void __launch_bounds__(128) k_sweep_strided2(const stream_args a) {
+  using E = cpx<float>;
+  constexpr int SLOT = (C + 1) * 32;  // float4 (two complex) per slot
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int R = a.ring;
+  if (R < 3 || R > 4 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT) * 16u) {
+    if (threadIdx.x == 0) atomicOr(a.flags, 2);
+    return;
+  }
+  float4* ring = reinterpret_cast<float4*>(smem_raw) + (size_t)wib * R * SLOT;
+  const long long ngroups = (a.nlines + 63) / 64;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  acc_t<float> acc;
+  if (wg < ngroups * a.nseg) {
+    const long long g = wg % ngroups;
+    const int sg = (int)(wg / ngroups);
+    const long long c0 = (g * 32 + lane) * 2;
+    const bool active = c0 < a.nlines;
+    const long long base = active ? (c0 / a.nx) * a.outer + (c0 % a.nx) : 0;
+    const E* in = static_cast<const E*>(a.in) + base;
+    E* out = static_cast<E*>(a.out) + base;
+    const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
+    const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
+    const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
+    const coef5<float>* crow[2];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int li = (a.coef_mode == 1 && active) ? (int)((c0 + v) % a.nx) : 0;
+      crow[v] = static_cast<const coef5<float>*>(a.coef) + (size_t)li * (lt + 1);
+    }
+    const coef2 cf = make_coef2(crow[0][lt], crow[1][lt]);
+    auto slot = [&](int q) { return ring + (size_t)(q % R) * SLOT + lane; };
+    auto issue = [&](int q) {
+      if (q < qb) {
+        float4* sl = slot(q);
+#pragma unroll
+        for (int r = 0; r <= C; ++r) {
+          const int p = q * C + r;
+          if (active && p < N)
+            cp_async<16>(&sl[r * 32], in + (long long)p * a.stride);
+          else
+            sl[r * 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      cp_async_commit();
+    };
+    for (int i = 0; i < R - 1; ++i) issue(qa + i);
+    c2 pm = zero2(), d = zero2();
+    for (int q = qa; q <= qb; ++q) {
+      if (q < qb) {
+        ring_wait(R);
+        if (q * C >= lt && (q + 1) * C <= N)
+          strided_forward2<C, true>(slot(q), pm, d, crow, cf, q * C, lt);
+        else
+          strided_forward2<C, false>(slot(q), pm, d, crow, cf, q * C, lt);
+      }
+      const int qq = q - 1;
+      if (qq >= qo0 && qq < qo1) {
+        c2 x = zero2();
+        const int la = min(a.halo, N - q * C);
+        const float4* sq = slot(q);
+        const bool la_fast = q * C >= lt;
+        for (int h = la - 1; h >= 0; --h) {
+          k2 be = cf.be;
+          if (!la_fast) {
+            const int i = min(q * C + h, lt);
+            be = make_k2(crow[0][i].be, crow[1][i].be);
+          }
+          x = kfma2(be, x, unpack_split(sq[h * 32]));
+        }
+        const float4* sp = slot(qq);
+        const bool fast = qq * C >= lt && q * C <= N;
+        auto back = [&](auto fast_tag) {
+          constexpr bool FAST = decltype(fast_tag)::value;
+          float4 w[C];
+#pragma unroll
+          for (int r = 0; r < C; ++r) w[r] = sp[r * 32];
+#pragma unroll
+          for (int r = C - 1; r >= 0; --r) {
+            const int p = qq * C + r;
+            if (!FAST && p >= N) continue;
+            k2 be;
+            if (FAST) {
+              be = cf.be;
+            } else {
+              const int i = min(p, lt);
+              be = make_k2(crow[0][i].be, crow[1][i].be);
+            }
+            x = kfma2(be, x, unpack_split(w[r]));
+            if (REDUCE) {
+              const float2 n2 = __ffma2_rn(x.im, x.im, __fmul2_rn(x.re, x.re));
+              acc.add(n2.x + n2.y);
+            }
+            if (active) *reinterpret_cast<float4*>(out + (long long)p * a.stride) = join2(x);
+          }
+        };
+        if (fast)
+          back(bool_tag<true>{});
+        else
+          back(bool_tag<false>{});
+      }
+      issue(q + R - 1);
+    }
+    cp_async_wait<0>();
+  }
+  if (REDUCE) norm_epilogue(acc.value(), a);
+}
+
 // --------------------------------------------------------------- launchers
 cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis_coef& co,
                           cudaStream_t s) {
@@ -301,6 +376,17 @@ static cudaError_t dispatch_s(bool reduce, const stream_args& a, const sweep_sha
   return cudaGetLastError();
 }
 
+template <int C>
+static cudaError_t dispatch_s2(bool reduce, const stream_args& a, const sweep_shape& sh,
+                               cudaStream_t s) {
+  static bool done[2] = {false, false};
+  auto fn = reduce ? k_sweep_strided2<C, true> : k_sweep_strided2<C, false>;
+  cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 // Every (precision, V, C) combination the host can choose is instantiated
 // here; anything else is rejected before a launch.
 cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
@@ -310,8 +396,8 @@ cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
     if (sh.V == 1 && sh.C == 64) return dispatch_s<double, 1, 64>(reduce, a, sh, s);
     return cudaErrorInvalidValue;
   }
-  if (sh.V == 2 && sh.C == 8) return dispatch_s<float, 2, 8>(reduce, a, sh, s);
-  if (sh.V == 2 && sh.C == 16) return dispatch_s<float, 2, 16>(reduce, a, sh, s);
+  if (sh.V == 2 && sh.C == 8) return dispatch_s2<8>(reduce, a, sh, s);
+  if (sh.V == 2 && sh.C == 16) return dispatch_s2<16>(reduce, a, sh, s);
   if (sh.V == 1 && sh.C == 16) return dispatch_s<float, 1, 16>(reduce, a, sh, s);
   if (sh.V == 1 && sh.C == 64) return dispatch_s<float, 1, 64>(reduce, a, sh, s);
   return cudaErrorInvalidValue;

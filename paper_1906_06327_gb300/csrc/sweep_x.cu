@@ -225,6 +225,222 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
   cp_async_wait<0>();
 }
 
+// Complex float, two rows per lane (rows lane and lane + 32): the same
+// pipeline with the two rows in split form, so that H1 and the recurrences
+// run as packed FP32x2 arithmetic (sweep_common.cuh).  The ring keeps each
+// row interleaved (the cooperative copies and stores need that); rows are
+// split on the 16-byte shared loads and joined on the stores.
+template <int C, bool IMAG, bool VEC16>
+__global__ void __launch_bounds__(128) k_sweep_x2(const stream_args a) {
+  using E = cpx<float>;
+  constexpr int EP = VEC16 ? 2 : 1;
+  constexpr int PITCH = C + 2;                 // odd number of 16-byte units
+  constexpr int ROWS = 64;
+  constexpr int SLOT = ROWS * PITCH;
+  constexpr int LPR = (C + 1 + EP - 1) / EP;
+  constexpr int SPR = C / EP;
+  static_assert(LPR * EP <= PITCH, "row pitch too small");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int R = a.ring;
+  if (R < 3 || R > 4 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT) * (unsigned)sizeof(E)) {
+    if (threadIdx.x == 0) atomicOr(a.flags, 2);
+    return;
+  }
+  E* ring = reinterpret_cast<E*>(smem_raw) + (size_t)wib * R * SLOT;
+  const long long nrows = a.nlines;
+  const long long ngroups = (nrows + ROWS - 1) / ROWS;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= ngroups * a.nseg) return;  // whole warp; no block barrier below
+  const long long g = wg % ngroups;
+  const int sg = (int)(wg / ngroups);
+  const long long row0 = g * ROWS;
+  const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
+  const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
+  const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
+  const E* in = static_cast<const E*>(a.in);
+  E* out = static_cast<E*>(a.out);
+
+  const coef5<float>* crow[2];
+  float vyz[2];
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    const long long rr = row0 + lane + 32 * v;
+    const bool act = rr < nrows;
+    const int j = act ? (int)(rr % a.ny) : 0;
+    const int k = act ? (int)(rr / a.ny) : 0;
+    crow[v] = static_cast<const coef5<float>*>(a.coef) + (size_t)j * (lt + 1);
+    const float y = (float)(a.y0 + (double)j * a.hy), z = (float)(a.z0 + (double)k * a.hz);
+    vyz[v] = (float)a.hnu2 * y * y + (float)a.hlam2 * z * z;
+  }
+  const coef2 cf = make_coef2(crow[0][lt], crow[1][lt]);
+  const float s = (float)(*a.scale), hg2 = (float)a.hgam2, dt = (float)a.dt;
+  const float2 S2 = make_float2(s, s), G2 = make_float2((float)a.g, (float)a.g);
+  const float2 VYZ = make_float2(vyz[0], vyz[1]);
+  const float xs = (float)a.x0, hx = (float)a.hx;
+  // psi of both rows at position p: scaled and advanced by H1
+  auto h1 = [&](c2 v, int p) -> c2 {
+    v.re = __fmul2_rn(S2, v.re);
+    v.im = __fmul2_rn(S2, v.im);
+    const float x = xs + (float)p * hx;
+    const float vx = hg2 * x * x;
+    const float2 dens = __ffma2_rn(v.im, v.im, __fmul2_rn(v.re, v.re));
+    const float2 en = __ffma2_rn(G2, dens, __fadd2_rn(VYZ, make_float2(vx, vx)));
+    if (IMAG) {
+      const float2 f = make_float2(__expf(-dt * en.x), __expf(-dt * en.y));
+      v.re = __fmul2_rn(f, v.re);
+      v.im = __fmul2_rn(f, v.im);
+    } else {
+      float2 sn, cs;
+      sincosf(dt * en.x, &sn.x, &cs.x);
+      sincosf(dt * en.y, &sn.y, &cs.y);
+      const float2 re = __ffma2_rn(sn, v.im, __fmul2_rn(cs, v.re));
+      v.im = __ffma2_rn(make_float2(-sn.x, -sn.y), v.re, __fmul2_rn(cs, v.im));
+      v.re = re;
+    }
+    return v;
+  };
+  auto slot = [&](int q) { return ring + (size_t)(q % R) * SLOT; };
+  auto issue = [&](int q) {
+    if (q < qb) {
+      E* sl = slot(q);
+      for (int t = lane; t < ROWS * LPR; t += 32) {
+        const int row = t / LPR, col = t % LPR;
+        const int p = q * C + col * EP;
+        const long long rr = row0 + row;
+        E* dst = sl + row * PITCH + col * EP;
+        if (rr < nrows && p < N) {
+          cp_async<EP * sizeof(E)>(dst, in + rr * N + p);
+        } else {
+#pragma unroll
+          for (int e = 0; e < EP; ++e) dst[e] = zero<float>();
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // points 2k, 2k+1 of both lane rows, split; and the inverse
+  auto load_pair = [&](const E* sl, int k, c2& e0, c2& e1) {
+    const float4 u = reinterpret_cast<const float4*>(sl + lane * PITCH)[k];
+    const float4 w = reinterpret_cast<const float4*>(sl + (lane + 32) * PITCH)[k];
+    e0.re = make_float2(u.x, w.x);
+    e0.im = make_float2(u.y, w.y);
+    e1.re = make_float2(u.z, w.z);
+    e1.im = make_float2(u.w, w.w);
+  };
+  auto store_pair = [&](E* sl, int k, const c2& e0, const c2& e1) {
+    reinterpret_cast<float4*>(sl + lane * PITCH)[k] = make_float4(e0.re.x, e0.im.x, e1.re.x, e1.im.x);
+    reinterpret_cast<float4*>(sl + (lane + 32) * PITCH)[k] =
+        make_float4(e0.re.y, e0.im.y, e1.re.y, e1.im.y);
+  };
+  auto coef_p = [&](auto fast_tag, int p) -> coef2 {
+    if (decltype(fast_tag)::value) return cf;
+    const int i = min(p, lt);
+    return make_coef2(crow[0][i], crow[1][i]);
+  };
+  // forward sweep over one chunk: stage the lane's two rows (and the next
+  // point) in registers, advance them by H1, solve, write d' back
+  auto forward = [&](auto fast_tag, E* s0, int p0, c2& pm, c2& d) {
+    c2 w[C + 1];
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) load_pair(s0, k, w[2 * k], w[2 * k + 1]);
+    w[C].re = make_float2(s0[lane * PITCH + C].x, s0[(lane + 32) * PITCH + C].x);
+    w[C].im = make_float2(s0[lane * PITCH + C].y, s0[(lane + 32) * PITCH + C].y);
+#pragma unroll
+    for (int r = 0; r <= C; ++r) w[r] = h1(w[r], p0 + r);
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      const c2 pc = w[r];
+      d = fwd2(coef_p(fast_tag, p0 + r), pm, pc, w[r + 1], d);
+      pm = pc;
+      w[r] = d;
+    }
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) store_pair(s0, k, w[2 * k], w[2 * k + 1]);
+  };
+  // back substitution over chunk slot sp (positions p0..p0+C-1), x carried in
+  auto backward = [&](auto fast_tag, E* sp, int p0, c2& x) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    c2 w[C];
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) load_pair(sp, k, w[2 * k], w[2 * k + 1]);
+#pragma unroll
+    for (int r = C - 1; r >= 0; --r) {
+      if (FAST || p0 + r < N) x = kfma2(coef_p(fast_tag, p0 + r).be, x, w[r]);
+      w[r] = x;
+    }
+#pragma unroll
+    for (int k = 0; k < C / 2; ++k) store_pair(sp, k, w[2 * k], w[2 * k + 1]);
+  };
+
+  for (int i = 0; i < R - 1; ++i) issue(qa + i);
+  c2 pm = zero2(), d = zero2();
+  for (int q = qa; q <= qb; ++q) {
+    if (q < qb) {
+      ring_wait(R);
+      __syncwarp();
+      if (q * C >= lt && (q + 1) * C <= N)
+        forward(bool_tag<true>{}, slot(q), q * C, pm, d);
+      else
+        forward(bool_tag<false>{}, slot(q), q * C, pm, d);
+    }
+    const int qq = q - 1;
+    if (qq >= qo0 && qq < qo1) {
+      c2 x = zero2();
+      const int la = min(a.halo, N - q * C);
+      const E* sq = slot(q);
+      const bool la_fast = q * C >= lt;
+      for (int h = la - 1; h >= 0; --h) {
+        k2 be = cf.be;
+        if (!la_fast) {
+          const int i = min(q * C + h, lt);
+          be = make_k2(crow[0][i].be, crow[1][i].be);
+        }
+        c2 t;
+        t.re = make_float2(sq[lane * PITCH + h].x, sq[(lane + 32) * PITCH + h].x);
+        t.im = make_float2(sq[lane * PITCH + h].y, sq[(lane + 32) * PITCH + h].y);
+        x = kfma2(be, x, t);
+      }
+      E* sp = slot(qq);
+      if (qq * C >= lt && q * C <= N)
+        backward(bool_tag<true>{}, sp, qq * C, x);
+      else
+        backward(bool_tag<false>{}, sp, qq * C, x);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < ROWS * SPR / 32; ++i) {
+        const int t = i * 32 + lane;
+        const int row = t / SPR, col = t % SPR;
+        const int p = qq * C + col * EP;
+        const long long rr = row0 + row;
+        if (rr < nrows && p < N) {
+          const E* src = sp + row * PITCH + col * EP;
+          if (EP == 2)
+            *reinterpret_cast<float4*>(out + rr * N + p) = *reinterpret_cast<const float4*>(src);
+          else
+            out[rr * N + p] = *src;
+        }
+      }
+    }
+    __syncwarp();
+    issue(q + R - 1);
+  }
+  cp_async_wait<0>();
+}
+
+template <int C>
+static cudaError_t dispatch_x2(bool imag, bool vec16, const stream_args& a, const sweep_shape& sh,
+                               cudaStream_t s) {
+  static bool done[4] = {false, false, false, false};
+  auto fn = vec16 ? (imag ? k_sweep_x2<C, true, true> : k_sweep_x2<C, false, true>)
+                  : (imag ? k_sweep_x2<C, true, false> : k_sweep_x2<C, false, false>);
+  cudaError_t e = allow_smem((const void*)fn, &done[(vec16 ? 2 : 0) + (imag ? 1 : 0)]);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class T, int V, int C>
 static cudaError_t dispatch_x(bool imag, bool vec16, const stream_args& a, const sweep_shape& sh,
                               cudaStream_t s) {
@@ -246,8 +462,8 @@ cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const swe
     if (sh.V == 1 && sh.C == 64) return dispatch_x<double, 1, 64>(imag, true, a, sh, s);
     return cudaErrorInvalidValue;
   }
-  if (sh.V == 2 && sh.C == 8) return dispatch_x<float, 2, 8>(imag, sh.vec16, a, sh, s);
-  if (sh.V == 2 && sh.C == 16) return dispatch_x<float, 2, 16>(imag, sh.vec16, a, sh, s);
+  if (sh.V == 2 && sh.C == 8) return dispatch_x2<8>(imag, sh.vec16, a, sh, s);
+  if (sh.V == 2 && sh.C == 16) return dispatch_x2<16>(imag, sh.vec16, a, sh, s);
   if (sh.V == 1 && sh.C == 16) return dispatch_x<float, 1, 16>(imag, sh.vec16, a, sh, s);
   if (sh.V == 1 && sh.C == 64) return dispatch_x<float, 1, 64>(imag, sh.vec16, a, sh, s);
   return cudaErrorInvalidValue;

@@ -24,6 +24,8 @@ ROTGP_ENONFINITE = -4
 ROTGP_EUNSUPPORTED = -5
 ROTGP_FP64 = 0
 ROTGP_FP32 = 1
+ROTGP_SOLVER_THOMAS = 0
+ROTGP_SOLVER_STENCIL = 1
 
 ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECUDA",
                ROTGP_ENONFINITE: "ENONFINITE", ROTGP_EUNSUPPORTED: "EUNSUPPORTED"}
@@ -32,7 +34,8 @@ ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECU
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
            "rotgp_set_omega", "rotgp_init_analytic", "rotgp_set_psi", "rotgp_get_psi",
            "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
-           "rotgp_info", "rotgp_tune", "rotgp_profile_enable", "rotgp_profile_read",
+           "rotgp_info", "rotgp_tune", "rotgp_set_solver", "rotgp_profile_enable",
+           "rotgp_profile_read",
            "rotgp_observables_noalloc")
 
 
@@ -63,6 +66,7 @@ class SolverInfo(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("halo", ctypes.c_int), ("table_len", ctypes.c_int),
                 ("chunk", ctypes.c_int * 3), ("segments", ctypes.c_int * 3),
                 ("lines_per_lane", ctypes.c_int * 3), ("ring", ctypes.c_int * 3),
+                ("stencil_taps", ctypes.c_int * 3),
                 ("warps_per_block", ctypes.c_int * 3),
                 ("decay", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
 
@@ -111,6 +115,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_sync.argtypes = [vp]
         lib.rotgp_info.argtypes = [vp, ctypes.POINTER(SolverInfo)]
         lib.rotgp_tune.argtypes = [vp, ip, ip, ip, ip, ip, ip]
+        lib.rotgp_set_solver.argtypes = [vp, ip, ip]
         lib.rotgp_profile_enable.argtypes = [vp, ip]
         lib.rotgp_profile_read.argtypes = [vp, ctypes.POINTER(KStat), ip, ctypes.POINTER(ip)]
         lib.rotgp_observables_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Phys), ip,
@@ -240,6 +245,11 @@ class Solver:
              segments: int):
         self._check(self._lib.rotgp_tune(self._h, int(axis), int(lines_per_lane), int(chunk),
                                          int(ring), int(warps_per_block), int(segments)))
+
+    def set_solver(self, axis: int, solver: str):
+        """solver: "thomas" or "stencil" (see rotgp_set_solver)."""
+        code = {"thomas": ROTGP_SOLVER_THOMAS, "stencil": ROTGP_SOLVER_STENCIL}[solver]
+        self._check(self._lib.rotgp_set_solver(self._h, int(axis), code))
 
     # -- timing
     def profile(self, on: bool = True):

@@ -273,3 +273,32 @@ def test_3d_256x256x128_fp32_two_steps_full_grid():
     refo = oracle.observables(grid, phys, ref)
     for k in OBS_REL:
         assert abs(ob[k] - refo[k]) <= 1e-5 * abs(refo[k]), k
+
+
+# ------------------------------------------------------------------ solver forms
+@pytest.mark.parametrize("n,h", [((100, 64), (0.12, 0.15)), ((132, 36), (0.1, 0.3)),
+                                 ((44, 36, 40), (0.3, 0.3, 0.25))])
+@pytest.mark.parametrize("imag", [True, False])
+def test_stencil_form_matches_thomas_fp32(n, h, imag):
+    """The banded-inverse stencil and the Thomas solve are the same CN
+    substep: same state after 20 steps up to float rounding."""
+    phys = dict(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3)
+    R = inputs.random_phase_field(n[0], n[1], 8)
+    a = Solver(n, h, precision="fp32", **phys)
+    b = Solver(n, h, precision="fp32", **phys)
+    info = a.info()
+    assert all(t > 0 for t in info["stencil_taps"]), info
+    for axis in range(len(n)):
+        b.set_solver(axis, "thomas")
+    assert all(t == 0 for t in b.info()["stencil_taps"])
+    for s in (a, b):
+        s.init_analytic(1, R, 1.0, 1.0)
+        (s.step_imag if imag else s.step_real)(20)
+    pa, pb = a.get_psi(), b.get_psi()
+    # float rounding of two evaluation orders over 20 steps of a rough
+    # random-phase state (the stencil's truncated tail is below 2e-10)
+    assert np.max(np.abs(pa - pb)) <= 5e-6 * np.max(np.abs(pb))
+    grid = Grid(n, h)
+    ref, _ = oracle.steps(grid, Phys(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3),
+                          oracle.init_analytic(grid, 1, R), 20, imag)
+    assert np.max(np.abs(pa - ref)) <= 5e-6 * np.max(np.abs(ref))

@@ -46,6 +46,7 @@ extern "C" {
 #define ROTGP_ENONFINITE (-4)   /* NaN/Inf norm seen by the step reduction   */
 #define ROTGP_EUNSUPPORTED (-5) /* line systems too weakly diagonally
                                    dominant for the chunked line solver      */
+#define ROTGP_ETIMEOUT (-6)     /* a bounded device wait (TMA load) ran out  */
 
 #define ROTGP_FP64 0 /* complex double throughout                           */
 #define ROTGP_FP32 1 /* complex float bulk; norm, energy, mu, rms in double  */
@@ -110,6 +111,8 @@ typedef struct {
   int stencil_taps[3];    /* taps of the banded-inverse stencil in use,
                              0 when the axis uses the Thomas solve        */
   int warps_per_block[3];
+  int fused_xy;           /* 1: H1 and the x and y sweeps run as one tile
+                             pass (ROTGP_SOLVER_FUSED)                    */
   double decay;           /* largest per-point decay of a truncated carry */
   size_t device_bytes;    /* device memory owned by the context           */
 } rotgp_solver_info;
@@ -185,10 +188,19 @@ int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring
  *   geometrically away from the diagonal; the dropped tail is below 2e-10
  *   of the largest weight and the end rows of each line are exact).
  *   Complex float only, and only where rotgp_info reports stencil taps at
- *   create time (ROTGP_EUNSUPPORTED otherwise).  The default wherever it
- *   is available. */
+ *   create time (ROTGP_EUNSUPPORTED otherwise).
+ * ROTGP_SOLVER_FUSED (axis 0 or 1): H1 and the x and y sweeps, both in
+ *   stencil form, as one pass over each z plane in tiles with K-point
+ *   halos (the result equals the separate stencil sweeps up to float
+ *   rounding).  In 2D it is the whole step.  Selecting THOMAS or STENCIL
+ *   on axis 0 or 1 turns it off.
+ * A new context uses ROTGP_SOLVER_THOMAS on every axis. 
+ * The y and z sweeps in stencil form, and the fused pass, stage their
+ * tiles with TMA loads whose waits are bounded: a wait that runs out
+ * (about 2 s) makes the next synchronising call return ROTGP_ETIMEOUT. */
 #define ROTGP_SOLVER_THOMAS 0
 #define ROTGP_SOLVER_STENCIL 1
+#define ROTGP_SOLVER_FUSED 2
 int rotgp_set_solver(rotgp_ctx* ctx, int axis, int solver);
 
 /* Per-kernel CUDA-event timing.  While enabled, every kernel launch of the

@@ -97,6 +97,29 @@ struct stream_args {
   int* flags;
 };
 
+// Tile passes (tiles_xy.cu, tiles_line.cu), complex float only.
+struct tile_args {
+  void* out;             // the other state buffer
+  const void* wx;        // banded-inverse weights, [line][2B+1][2K+1] complex float
+  const void* wy;
+  const void* wz;
+  int nx, ny, nz;        // stored points per axis
+  int bx, by, bz;        // end rows with their own weights, per axis
+  int tiles_x, tiles_y;  // xy pass: tiles per plane; line pass: patches across the lines
+  // H1 substep and the pending scale (xy pass)
+  float dt, g, hgam2, hnu2, hlam2;
+  float x0, hx, y0, hy, z0, hz;
+  const double* scale;
+  // norm reduction in the last pass of a step
+  double vol;
+  int imag;
+  double* partials;
+  unsigned int* counter;
+  double* scale_out;
+  double* norm_out;
+  int* flags;            // bit 0 non-finite norm, bit 2 TMA wait timed out
+};
+
 struct obs_args {
   const void* psi;
   int nx, ny, nz, dim;
@@ -145,11 +168,19 @@ size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);
 cudaError_t launch_stencil_tables(void* wtab, int nlines, int K, int B, int m,
                                   const axis_coef& co, cudaStream_t s);
 cudaError_t launch_stencil_x(bool imag, const stream_args& a, long long warps, cudaStream_t s);
-cudaError_t launch_stencil_strided(bool reduce, const stream_args& a, long long warps,
-                                   int wpb, cudaStream_t s);
 inline bool stencil_k_built(int K) { return K == 4 || K == 6 || K == 8; }
-// blocks of the strided stencil launch (tasks of 64 columns x 16 points)
-long long stencil_strided_blocks(long long nlines, int len, int wpb);
+// Tile passes.  xy_tile_geometry gives the host the xy tile of stencil
+// reach K (TX x TY outputs, R rows and WX points per staged row);
+// line_rows the transverse rows of a line-pass CTA (32 x line_rows lines);
+// launch_* return cudaErrorInvalidValue for an unbuilt K (tile_k_built).
+bool tile_k_built(int K);
+unsigned xy_pass_smem(int K);  // dynamic shared memory of one xy-pass CTA
+void xy_tile_geometry(int K, int* TX, int* TY, int* R, int* WX);
+int line_rows();
+cudaError_t launch_xy_pass(bool imag, bool reduce, int K, const void* map, const tile_args& a,
+                           unsigned blocks, cudaStream_t s);
+cudaError_t launch_line_pass(int axis, bool reduce, int K, const void* map, const tile_args& a,
+                             unsigned blocks, cudaStream_t s);
 // Is (precision, V, C) one of the instantiated sweep kernels?
 inline bool sweep_shape_built(bool fp64, int V, int C) {
   if (fp64) return V == 1 && (C == 16 || C == 64);

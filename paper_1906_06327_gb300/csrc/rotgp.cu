@@ -7,11 +7,15 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/rotgp.h"
 #include "common.cuh"
+#include "tma.cuh"
 
 using namespace rotgp;
 
@@ -24,12 +28,12 @@ constexpr int kMaxTable = 512;
 
 enum KernelId {
   K_SWEEP_X, K_SWEEP_Y, K_SWEEP_Z, K_OBS, K_VMOM, K_VCOUNT, K_NORM, K_INIT, K_IO, K_TABLES,
-  K_COUNT
+  K_XY, K_COUNT
 };
-const char* kKernelNames[K_COUNT] = {"sweep_x_h1", "sweep_y",        "sweep_z",
+const char* kKernelNames[K_COUNT] = {"sweep_x_h1",  "sweep_y",        "sweep_z",
                                      "observables", "vortex_moments", "vortex_count",
                                      "norm",        "init_analytic",  "pack_unpack",
-                                     "tables"};
+                                     "tables",      "xy_pass_h1"};
 
 struct AxisPlan {
   int nlines = 0;       // lines with distinct coefficients (table rows)
@@ -43,7 +47,7 @@ struct AxisPlan {
   // banded-inverse stencil (complex float): taps K, end rows B, weights [mode]
   bool stencil_ok = false;  // stencil form available for this axis
   bool use_stencil = false;
-  int sK = 0, sB = 0, snseg = 1, swpb = 1;
+  int sK = 0, sB = 0;
   void* wtab[2] = {nullptr, nullptr};
 };
 
@@ -74,6 +78,11 @@ struct rotgp_ctx {
   size_t staging_bytes = 0;
   double* dR = nullptr;
   AxisPlan axis[3];
+  // tile passes (complex float): H1 + x + y in one pass over each plane
+  // (fuse_xy), and the y/z stencil sweeps; TMA maps per state buffer
+  bool maps_ok = false;
+  bool fuse_ok = false, fuse_xy = false;
+  CUtensorMap map_xy[2], map_y[2], map_z[2];
   double* partials = nullptr;
   size_t partial_doubles = 0;
   unsigned* counter = nullptr;
@@ -328,12 +337,11 @@ int plan_axes(rotgp_ctx* c) {
     const long long groups = (ap.lines + 32 * V - 1) / (32 * V);
     int rc = set_shape(c, a, V, C, R, 1, std::max<long long>(1, target / groups));
     if (rc) return rc == ROTGP_EINVAL ? fail(c, ROTGP_EUNSUPPORTED, "%s", c->err.c_str()) : rc;
-    // banded-inverse stencil: complex float, even N_x (two columns per lane),
-    // x lines a multiple of 4 points
+    // banded-inverse stencil: complex float, even N_x (TMA rows of 16-byte
+    // multiples; the separate x-stencil kernel also wants N_x % 4 == 0)
     int K = 0, B = 0;
     const bool sized = ap.wtab[0] != nullptr;  // tables already allocated
-    ap.stencil_ok = !c->fp64 && c->nx % 2 == 0 && (!x || ap.len % 4 == 0) &&
-                    plan_stencil(c, a, &K, &B);
+    ap.stencil_ok = !c->fp64 && c->nx % 2 == 0 && plan_stencil(c, a, &K, &B);
     if (sized) {
       // keep the allocated size; a larger K or B than needed is only more exact
       ap.stencil_ok = ap.stencil_ok && K <= ap.sK && B <= ap.sB;
@@ -343,13 +351,77 @@ int plan_axes(rotgp_ctx* c) {
     if (ap.stencil_ok) {
       ap.sK = K;
       ap.sB = B;
-      // strided stencil: independent tasks of 64 columns x 16 points
-      ap.swpb = 4;
-      ap.snseg = 1;
     }
-    ap.use_stencil = ap.stencil_ok;
+    // default: the Thomas form (the stencil and fused forms are selected by
+    // rotgp_set_solver or rotgp_autotune)
+    ap.use_stencil = false;
   }
+  // one pass for H1, x and y: both axes in stencil form with one reach K
+  // (the larger of the two; a longer stencil is only more exact)
+  AxisPlan &ax = c->axis[0], &ay = c->axis[1];
+  if (!ax.wtab[0] && ax.stencil_ok && ay.stencil_ok) {
+    const int K = std::max(ax.sK, ay.sK);
+    ax.sK = ay.sK = K;
+    c->fuse_ok = tile_k_built(K);
+    c->fuse_xy = false;
+  }
+  c->fuse_ok = c->fuse_ok && ax.stencil_ok && ay.stencil_ok;
+  c->fuse_xy = c->fuse_xy && c->fuse_ok;
   return ROTGP_OK;
+}
+
+// blocks of the tile passes: the xy pass is persistent, as many CTAs as fit
+// on the SMs (at most one per tile)
+unsigned xy_blocks(const rotgp_ctx* c) {
+  int TX, TY, R, WX;
+  xy_tile_geometry(c->axis[0].sK, &TX, &TY, &R, &WX);
+  const long long tiles = (long long)((c->nx + TX - 1) / TX) * ((c->ny + TY - 1) / TY) * c->nz;
+  const long long per_sm = std::max<long long>(
+      1, std::min<long long>(8, (228 * 1024) / (xy_pass_smem(c->axis[0].sK) + 2048)));
+  return (unsigned)std::min<long long>(tiles, per_sm * c->sm_count);
+}
+unsigned line_blocks(const rotgp_ctx* c, int axis) {
+  const int nt = axis == 1 ? c->nz : c->ny, rows = line_rows();
+  return (unsigned)(((c->nx + 31) / 32) * ((nt + rows - 1) / rows));
+}
+
+// Driver entry point of the tensor-map encoder, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// TMA maps of both state buffers for the tile passes; without them the
+// stencil form of y and z and the fused x-y pass are switched off.
+void build_maps(rotgp_ctx* c) {
+  c->maps_ok = false;
+  bool ok = !c->fp64 && c->nx % 2 == 0;
+  for (int b = 0; b < 2 && ok; ++b) {
+    if (c->fuse_ok) {
+      int TX, TY, R, WX;
+      xy_tile_geometry(c->axis[0].sK, &TX, &TY, &R, &WX);
+      ok = ok && encode_state_map(&c->map_xy[b], c->psi[b], c->nx, c->ny, c->nz, 2 * WX, R, 1) == 0;
+    }
+    const unsigned rows = (unsigned)line_rows();
+    ok = ok && encode_state_map(&c->map_y[b], c->psi[b], c->nx, c->ny, c->nz, 64, 8, rows) == 0;
+    ok = ok && encode_state_map(&c->map_z[b], c->psi[b], c->nx, c->ny, c->nz, 64, rows, 8) == 0;
+  }
+  c->maps_ok = ok;
+  if (!ok) {
+    c->fuse_ok = c->fuse_xy = false;
+    for (int a = 1; a < c->grid.dim; ++a) c->axis[a].stencil_ok = c->axis[a].use_stencil = false;
+  }
+  for (int a = 1; a < c->grid.dim; ++a)
+    if (!tile_k_built(c->axis[a].sK)) c->axis[a].stencil_ok = c->axis[a].use_stencil = false;
 }
 
 int reduce_blocks(const rotgp_ctx* c, long long n) {
@@ -408,6 +480,59 @@ int build_tables(rotgp_ctx* c) {
 }
 
 // --------------------------------------------------------------- one step
+tile_args make_tile_args(rotgp_ctx* c, bool imag) {
+  tile_args t{};
+  const int mode = imag ? 1 : 0;
+  t.out = c->psi[1 - c->cur];
+  t.wx = c->axis[0].wtab[mode];
+  t.wy = c->axis[1].wtab[mode];
+  t.wz = c->grid.dim == 3 ? c->axis[2].wtab[mode] : nullptr;
+  t.nx = c->nx;
+  t.ny = c->ny;
+  t.nz = c->nz;
+  t.bx = c->axis[0].sB;
+  t.by = c->axis[1].sB;
+  t.bz = c->grid.dim == 3 ? c->axis[2].sB : 0;
+  t.dt = (float)c->phys.dt;
+  t.g = (float)c->phys.g;
+  t.hgam2 = (float)(0.5 * c->phys.gamma * c->phys.gamma);
+  t.hnu2 = (float)(0.5 * c->phys.nu * c->phys.nu);
+  t.hlam2 = c->grid.dim == 3 ? (float)(0.5 * c->phys.lambda * c->phys.lambda) : 0.f;
+  t.x0 = (float)c->x0;
+  t.hx = (float)c->grid.h[0];
+  t.y0 = (float)c->y0;
+  t.hy = (float)c->grid.h[1];
+  t.z0 = (float)c->z0;
+  t.hz = c->grid.dim == 3 ? (float)c->grid.h[2] : 0.f;
+  t.scale = c->d_scale();
+  t.vol = c->vol;
+  t.imag = imag ? 1 : 0;
+  t.partials = c->partials;
+  t.counter = c->counter;
+  t.scale_out = c->d_scale();
+  t.norm_out = c->d_norm();
+  t.flags = c->d_flags();
+  return t;
+}
+
+// H1, x and y sweeps in one pass (the whole step in 2D)
+int xy_pass(rotgp_ctx* c, bool imag) {
+  tile_args t = make_tile_args(c, imag);
+  int TX, TY, R, WX;
+  xy_tile_geometry(c->axis[0].sK, &TX, &TY, &R, &WX);
+  t.tiles_x = (c->nx + TX - 1) / TX;
+  t.tiles_y = (c->ny + TY - 1) / TY;
+  cudaError_t e;
+  {
+    Timed tm(c, K_XY);
+    e = launch_xy_pass(imag, c->grid.dim == 2, c->axis[0].sK, &c->map_xy[c->cur], t, xy_blocks(c),
+                       c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "xy pass launch");
+  c->cur = 1 - c->cur;
+  return ROTGP_OK;
+}
+
 int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
   const int mode = imag ? 1 : 0;
   const AxisPlan& ap = c->axis[axis];
@@ -451,7 +576,7 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
     a.scale = c->d_scale();
     Timed t(c, K_SWEEP_X);
-    if (ap.use_stencil) {
+    if (ap.use_stencil && c->nx % 4 == 0) {
       const long long warps = ((ap.lines + 1) / 2) * ((ap.len + 127) / 128);
       e = launch_stencil_x(imag, a, warps, c->stream);
     } else {
@@ -463,8 +588,11 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.coef_mode = axis == 1 ? 1 : 0;
     Timed t(c, axis == 1 ? K_SWEEP_Y : K_SWEEP_Z);
     if (ap.use_stencil) {
-      a.nseg = ap.snseg;
-      e = launch_stencil_strided(last, a, 0, ap.swpb, c->stream);
+      tile_args ta = make_tile_args(c, imag);
+      ta.tiles_x = (c->nx + 31) / 32;
+      ta.tiles_y = ((axis == 1 ? c->nz : c->ny) + line_rows() - 1) / line_rows();
+      e = launch_line_pass(axis, last, ap.sK, axis == 1 ? &c->map_y[c->cur] : &c->map_z[c->cur],
+                           ta, line_blocks(c, axis), c->stream);
     } else {
       e = launch_sweep_strided(c->fp64, last, a, ap.sh, c->stream);
     }
@@ -479,7 +607,13 @@ int run_steps(rotgp_ctx* c, long long n, bool imag) {
   if (n < 0) return fail(c, ROTGP_EINVAL, "negative step count");
   for (long long s = 0; s < n; ++s) {
     for (int a = 0; a < c->grid.dim; ++a) {
-      int rc = sweep(c, a, imag, a == c->grid.dim - 1);
+      int rc;
+      if (a == 0 && c->fuse_xy) {
+        rc = xy_pass(c, imag);
+        ++a;  // the y sweep is part of the pass
+      } else {
+        rc = sweep(c, a, imag, a == c->grid.dim - 1);
+      }
       if (rc) return rc;
     }
     ++c->steps;
@@ -494,6 +628,7 @@ int check_flags(rotgp_ctx* c) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
   if (flags & 2) return fail(c, ROTGP_ECUDA, "a sweep kernel was launched with a shape it was not built for");
+  if (flags & 4) return fail(c, ROTGP_ETIMEOUT, "a tile pass gave up waiting for its TMA load");
   if (flags & 1) return fail(c, ROTGP_ENONFINITE, "non-finite or zero norm in a reduction");
   return ROTGP_OK;
 }
@@ -538,6 +673,19 @@ int dev_alloc(rotgp_ctx* c, void** p, size_t bytes) {
 }  // namespace
 
 namespace rotgp {
+int encode_state_map(CUtensorMap* map, void* base, int nx, int ny, int nz, unsigned box0,
+                     unsigned box1, unsigned box2) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn) return -1;
+  const cuuint64_t dims[3] = {2ull * (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {8ull * (cuuint64_t)nx, 8ull * (cuuint64_t)nx * (cuuint64_t)ny};
+  const cuuint32_t box[3] = {box0, box1, box2};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return (int)fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 // Message returned by rotgp_last_error(NULL) on this thread.
 void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
 }  // namespace rotgp
@@ -631,11 +779,12 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     for (int m = 0; m < 2 && !rc; ++m) rc = dev_alloc(c, &ap.wtab[m], bytes);
   }
   if (!rc) {
-    // the stencil form of the last sweep reduces the norm in its own blocks
-    const AxisPlan& last = c->axis[grid->dim - 1];
-    if (last.stencil_ok)
-      c->partial_doubles = std::max(
-          c->partial_doubles, (size_t)stencil_strided_blocks(last.lines, last.len, 1));
+    // the tile passes reduce the norm in their own blocks
+    if (c->fuse_ok && grid->dim == 2)
+      c->partial_doubles = std::max(c->partial_doubles, (size_t)xy_blocks(c));
+    const int la = grid->dim - 1;
+    if (c->axis[la].stencil_ok && tile_k_built(c->axis[la].sK))
+      c->partial_doubles = std::max(c->partial_doubles, (size_t)line_blocks(c, la));
   }
   if (!rc) rc = dev_alloc(c, (void**)&c->partials, c->partial_doubles * sizeof(double));
   if (!rc) rc = dev_alloc(c, (void**)&c->counter, sizeof(unsigned));
@@ -651,6 +800,7 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     if (e == cudaSuccess) e = launch_set_scalar(c->d_scale(), 1.0, c->stream);
     if (e != cudaSuccess) rc = cuda_fail(c, e, "initialise buffers");
   }
+  if (!rc) build_maps(c);
   if (!rc) rc = build_tables(c);
   if (!rc) {
     e = cudaStreamSynchronize(c->stream);
@@ -666,6 +816,7 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
   c->bytes_per_launch[K_SWEEP_X] = 2.0 * state;
   c->bytes_per_launch[K_SWEEP_Y] = 2.0 * state;
   c->bytes_per_launch[K_SWEEP_Z] = 2.0 * state;
+  c->bytes_per_launch[K_XY] = 2.0 * state;
   c->bytes_per_launch[K_OBS] = 1.0 * state;
   *out = c;
   return ROTGP_OK;
@@ -914,6 +1065,7 @@ int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
     out->warps_per_block[a] = on ? c->axis[a].sh.warps_per_block : 0;
   }
   out->table_len = c->lt;
+  out->fused_xy = c->fuse_xy ? 1 : 0;
   out->decay = c->decay;
   out->device_bytes = c->device_bytes;
   return ROTGP_OK;
@@ -932,21 +1084,28 @@ int rotgp_tune(rotgp_ctx* c, int axis, int lines_per_lane, int chunk, int ring,
     c->axis[axis] = keep;
     return rc;
   }
-  AxisPlan& ap = c->axis[axis];
-  ap.snseg = std::max(1, std::min(segments, std::max(1, ap.len / 16)));
-  ap.swpb = std::min(warps_per_block, 4);
   return ROTGP_OK;
 }
 
 int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
   if (!c) return ROTGP_EINVAL;
   if (axis < 0 || axis >= c->grid.dim) return fail(c, ROTGP_EINVAL, "axis out of range");
-  if (solver != ROTGP_SOLVER_THOMAS && solver != ROTGP_SOLVER_STENCIL)
+  if (solver != ROTGP_SOLVER_THOMAS && solver != ROTGP_SOLVER_STENCIL &&
+      solver != ROTGP_SOLVER_FUSED)
     return fail(c, ROTGP_EINVAL, "unknown solver %d", solver);
   AxisPlan& ap = c->axis[axis];
-  if (solver == ROTGP_SOLVER_STENCIL && !ap.stencil_ok)
+  if (solver == ROTGP_SOLVER_FUSED) {
+    if (axis > 1) return fail(c, ROTGP_EINVAL, "the fused pass covers the x and y sweeps only");
+    if (!c->fuse_ok)
+      return fail(c, ROTGP_EUNSUPPORTED, "no fused x-y pass for this context");
+    c->axis[0].use_stencil = c->axis[1].use_stencil = true;
+    c->fuse_xy = true;
+    return ROTGP_OK;
+  }
+  if (solver == ROTGP_SOLVER_STENCIL && (!ap.stencil_ok || (axis == 0 && c->nx % 4 != 0)))
     return fail(c, ROTGP_EUNSUPPORTED, "no stencil form for axis %d of this context", axis);
   ap.use_stencil = solver == ROTGP_SOLVER_STENCIL;
+  if (axis <= 1) c->fuse_xy = false;
   return ROTGP_OK;
 }
 

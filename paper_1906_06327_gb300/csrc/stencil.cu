@@ -18,12 +18,12 @@
 // Thomas solve up to the truncated tail (bounded by the host) and float
 // rounding.
 //
-// y and z sweeps: lane = two adjacent columns, each lane walks a segment of
-// its lines with the 2K+1 inputs of the current point in a register window
-// (unrolled by 2K+1 so that the window never moves).  x sweep: a warp stages
-// two rows of 128 + 2K points in shared memory with the pending scale and
-// the H1 substep (Eq. eq1) applied once per point, and each lane produces 4
-// consecutive points of both rows.
+// This file holds the weight tables and the x sweep on its own (used when
+// the y sweep is not in stencil form): a warp stages two rows of 128 + 2K
+// points in shared memory with the pending scale and the H1 substep (Eq.
+// eq1) applied once per point, and each lane produces 4 consecutive points
+// of both rows.  The y and z sweeps (tiles_line.cu) and the fused H1 + x + y
+// pass (tiles_xy.cu) use the same tables.
 #include <algorithm>
 
 #include "sweep_common.cuh"
@@ -105,89 +105,6 @@ cudaError_t launch_stencil_tables(void* wtab, int nlines, int K, int B, int m,
 __device__ __forceinline__ k2 wpair(const cpx<float>* w0, const cpx<float>* w1, int S, int r,
                                     int k) {
   return make_k2(w0[r * S + k], w1[r * S + k]);
-}
-// Table row of output position p of a line with N points.
-__device__ __forceinline__ int wrow(int p, int N, int B) {
-  return p < B ? p : (p >= N - B ? B + 1 + (N - 1 - p) : B);
-}
-
-// ----------------------------------------------------------------- y / z
-// A task is 64 columns (two per lane) x M consecutive output points of the
-// line.  Each lane issues all M + 2K loads of its columns before any
-// arithmetic (plenty of bytes in flight per warp), then produces its M
-// outputs.  Neighbouring tasks re-read the 2K halo points, from L2.
-template <int K, int M, bool REDUCE>
-__global__ void __launch_bounds__(128) k_stencil_strided(const stream_args a) {
-  using E = cpx<float>;
-  constexpr int S = 2 * K + 1;
-  constexpr int NI = M + 2 * K;  // inputs per lane and task
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int N = a.len, B = a.brows, NR = 2 * B + 1;
-  const int nruns = (N + M - 1) / M;
-  const long long ngroups = (a.nlines + 63) / 64;
-  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
-  acc_t<float> acc;
-  if (wg < ngroups * nruns) {
-    const long long g = wg / nruns;
-    const int run = (int)(wg - g * nruns);
-    const long long c0 = (g * 32 + lane) * 2;
-    const bool active = c0 < a.nlines;
-    const long long base = active ? (c0 / a.nx) * a.outer + (c0 % a.nx) : 0;
-    const long long st = a.stride;
-    const E* in = static_cast<const E*>(a.in) + base;
-    E* out = static_cast<E*>(a.out) + base;
-    const int p0 = run * M;
-    float4 v[NI];
-    const int q0 = p0 - K;
-    if (active && q0 >= 0 && q0 + NI <= N) {
-      const E* src = in + (long long)q0 * st;
-#pragma unroll
-      for (int i = 0; i < NI; ++i) v[i] = *reinterpret_cast<const float4*>(src + i * st);
-    } else {
-#pragma unroll
-      for (int i = 0; i < NI; ++i) {
-        const int q = q0 + i;
-        v[i] = (active && q >= 0 && q < N)
-                   ? *reinterpret_cast<const float4*>(in + (long long)q * st)
-                   : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    const int l0 = (a.coef_mode == 1 && active) ? (int)(c0 % a.nx) : 0;
-    const int l1 = (a.coef_mode == 1 && active) ? (int)((c0 + 1) % a.nx) : 0;
-    const E* w0 = static_cast<const E*>(a.wtab) + (size_t)l0 * NR * S;
-    const E* w1 = static_cast<const E*>(a.wtab) + (size_t)l1 * NR * S;
-    auto put = [&](int p, const c2& x) {
-      if (REDUCE) {
-        const float2 n2 = __ffma2_rn(x.im, x.im, __fmul2_rn(x.re, x.re));
-        acc.add(n2.x + n2.y);
-      }
-      if (active) *reinterpret_cast<float4*>(out + (long long)p * st) = join2(x);
-    };
-    if (p0 >= B && p0 + M <= N - B) {
-      k2 w[S];
-#pragma unroll
-      for (int k = 0; k < S; ++k) w[k] = wpair(w0, w1, S, B, k);
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        c2 x = kmul2(w[0], split2(v[m]));
-#pragma unroll
-        for (int k = 1; k < S; ++k) x = kfma2(w[k], split2(v[m + k]), x);
-        put(p0 + m, x);
-      }
-    } else {
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        const int p = p0 + m;
-        if (p >= N) break;
-        const int row = wrow(p, N, B);
-        c2 x = zero2();
-#pragma unroll
-        for (int k = 0; k < S; ++k) x = kfma2(wpair(w0, w1, S, row, k), split2(v[m + k]), x);
-        put(p, x);
-      }
-    }
-  }
-  if (REDUCE) norm_epilogue(acc.value(), a);
 }
 
 // ----------------------------------------------------------------- x
@@ -320,7 +237,7 @@ __global__ void __launch_bounds__(128) k_stencil_x(const stream_args a) {
       const int p = pl + m;
       c2 x = zero2();
       if (p < N) {
-        const int row = wrow(p, N, B);
+        const int row = stencil_row(p, N, B);
 #pragma unroll
         for (int kk = 0; kk < S; ++kk) x = kfma2(wpair(w0, w1, S, row, kk), win[m + kk], x);
       }
@@ -340,8 +257,6 @@ __global__ void __launch_bounds__(128) k_stencil_x(const stream_args a) {
 }
 
 // ----------------------------------------------------------------- launchers
-constexpr int kStencilRun = 16;  // outputs per lane and task, y/z sweeps
-
 cudaError_t launch_stencil_x(bool imag, const stream_args& a, long long /*warps*/,
                              cudaStream_t s) {
   const long long tasks = ((a.nlines + 1) / 2) * ((a.len + 127) / 128);
@@ -358,29 +273,6 @@ cudaError_t launch_stencil_x(bool imag, const stream_args& a, long long /*warps*
   ROTGP_SX(6)
   ROTGP_SX(8)
 #undef ROTGP_SX
-  return cudaErrorInvalidValue;
-}
-
-long long stencil_strided_blocks(long long nlines, int len, int wpb) {
-  const long long tasks = ((nlines + 63) / 64) * ((len + kStencilRun - 1) / kStencilRun);
-  return (tasks + wpb - 1) / wpb;
-}
-
-cudaError_t launch_stencil_strided(bool reduce, const stream_args& a, long long /*warps*/,
-                                   int wpb, cudaStream_t s) {
-  const unsigned blocks = (unsigned)stencil_strided_blocks(a.nlines, a.len, wpb);
-#define ROTGP_SS(KK)                                                              \
-  if (a.taps_k == KK) {                                                           \
-    if (reduce)                                                                   \
-      k_stencil_strided<KK, kStencilRun, true><<<blocks, 32 * wpb, 0, s>>>(a);    \
-    else                                                                          \
-      k_stencil_strided<KK, kStencilRun, false><<<blocks, 32 * wpb, 0, s>>>(a);   \
-    return cudaGetLastError();                                                    \
-  }
-  ROTGP_SS(4)
-  ROTGP_SS(6)
-  ROTGP_SS(8)
-#undef ROTGP_SS
   return cudaErrorInvalidValue;
 }
 

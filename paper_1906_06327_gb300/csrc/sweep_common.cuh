@@ -137,7 +137,8 @@ struct acc_t<double> {
 // Block sum of v -> per-block partial; the last block to finish sums the
 // partials in block order (deterministic), sets the norm, the pending scale
 // (1/sqrt(norm) in imaginary time, 1 in real time) and the non-finite flag.
-static __device__ void norm_epilogue(double v, const stream_args& a) {
+template <class A>
+static __device__ void norm_epilogue(double v, const A& a) {
   __shared__ double ws[32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -253,6 +254,42 @@ __device__ __forceinline__ c2 unpack_split(const float4& t) {
   r.re = make_float2(t.x, t.y);
   r.im = make_float2(t.z, t.w);
   return r;
+}
+
+// ---------------------------------------------------------------- stencil form
+// Table row of output position p of a line with N points and B end rows at
+// each end: rows r < B are the left end (position r; row 0, the zero edge,
+// has no weights), row B the interior, row B + 1 + e the right end
+// (position N - 1 - e).
+__device__ __forceinline__ int stencil_row(int p, int N, int B) {
+  return p < B ? p : (p >= N - B ? B + 1 + (N - 1 - p) : B);
+}
+
+// Complex multiply-accumulate on the interleaved (re, im) layout: with
+// w = wr + i wi, a += (wr, wr) * v and b += (wi, wi) * v; the sum is then
+// (a.x - b.y, a.y + b.x).  Two independent packed FP32x2 chains, and the
+// operands are used as they are stored.
+struct cacc {
+  float2 a, b;
+};
+__device__ __forceinline__ cacc cacc_zero() {
+  cacc c;
+  c.a = make_float2(0.f, 0.f);
+  c.b = make_float2(0.f, 0.f);
+  return c;
+}
+__device__ __forceinline__ void cmac(cacc& c, const float2& wr, const float2& wi,
+                                     const float2& v) {
+  c.a = __ffma2_rn(wr, v, c.a);
+  c.b = __ffma2_rn(wi, v, c.b);
+}
+__device__ __forceinline__ float2 cfin(const cacc& c) {
+  return make_float2(c.a.x - c.b.y, c.a.y + c.b.x);
+}
+// a complex weight as the two duplicated pairs (wr, wr), (wi, wi)
+__device__ __forceinline__ void wsplit(const float2& w, float2& wr, float2& wi) {
+  wr = make_float2(w.x, w.x);
+  wi = make_float2(w.y, w.y);
 }
 
 }  // namespace rotgp

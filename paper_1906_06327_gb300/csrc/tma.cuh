@@ -1,0 +1,83 @@
+// tma.cuh -- tensor-memory-accelerator loads and shared-memory barriers
+// (inline PTX, sm_100 family) for the tile kernels of tiles_xy.cu and
+// tiles_line.cu, plus the host-side tensor-map encoder.
+//
+// A CTA's thread 0 initialises an mbarrier, arms it with the byte count of
+// the box, and issues cp.async.bulk.tensor; the box lands in shared memory
+// (elements outside the tensor read as zero) and completes the barrier's
+// transaction count.  Every thread then waits on the barrier's phase with a
+// bounded wait: after ~2 s of device time it gives up and reports a timeout
+// instead of spinning forever.
+#pragma once
+
+#include <cuda.h>
+#include <cstdint>
+
+namespace rotgp {
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+// make initialised barriers visible to the async (TMA) proxy
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier; false after ~2 s (or 2^26 polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (int i = 0; i < (1 << 26); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+    if (clock64() - t0 > 4000000000LL) break;
+  }
+  return false;
+}
+
+// 3-D tiled TMA load of the box at element coordinates (c0, c1, c2) into
+// shared memory (16-byte aligned start in c0 is the caller's duty).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Host: encode a 3-D float32 tensor map over a complex-float state of
+// nx x ny x nz points (x fastest; dimension 0 counts floats, 2 per point)
+// with the given box (floats, rows, planes).  Returns a CUDA driver status
+// (0 = success); -1 if the encoder entry point is unavailable.
+int encode_state_map(CUtensorMap* map, void* base, int nx, int ny, int nz, unsigned box0,
+                     unsigned box1, unsigned box2);
+
+}  // namespace rotgp

@@ -22,13 +22,16 @@ ROTGP_ENOMEM = -2
 ROTGP_ECUDA = -3
 ROTGP_ENONFINITE = -4
 ROTGP_EUNSUPPORTED = -5
+ROTGP_ETIMEOUT = -6
 ROTGP_FP64 = 0
 ROTGP_FP32 = 1
 ROTGP_SOLVER_THOMAS = 0
 ROTGP_SOLVER_STENCIL = 1
+ROTGP_SOLVER_FUSED = 2
 
 ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECUDA",
-               ROTGP_ENONFINITE: "ENONFINITE", ROTGP_EUNSUPPORTED: "EUNSUPPORTED"}
+               ROTGP_ENONFINITE: "ENONFINITE", ROTGP_EUNSUPPORTED: "EUNSUPPORTED",
+               ROTGP_ETIMEOUT: "ETIMEOUT"}
 
 # Every entry point declared in include/rotgp.h.
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
@@ -67,7 +70,7 @@ class SolverInfo(ctypes.Structure):
                 ("chunk", ctypes.c_int * 3), ("segments", ctypes.c_int * 3),
                 ("lines_per_lane", ctypes.c_int * 3), ("ring", ctypes.c_int * 3),
                 ("stencil_taps", ctypes.c_int * 3),
-                ("warps_per_block", ctypes.c_int * 3),
+                ("warps_per_block", ctypes.c_int * 3), ("fused_xy", ctypes.c_int),
                 ("decay", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
 
 
@@ -247,8 +250,9 @@ class Solver:
                                          int(ring), int(warps_per_block), int(segments)))
 
     def set_solver(self, axis: int, solver: str):
-        """solver: "thomas" or "stencil" (see rotgp_set_solver)."""
-        code = {"thomas": ROTGP_SOLVER_THOMAS, "stencil": ROTGP_SOLVER_STENCIL}[solver]
+        """solver: "thomas", "stencil" or "fused" (see rotgp_set_solver)."""
+        code = {"thomas": ROTGP_SOLVER_THOMAS, "stencil": ROTGP_SOLVER_STENCIL,
+                "fused": ROTGP_SOLVER_FUSED}[solver]
         self._check(self._lib.rotgp_set_solver(self._h, int(axis), code))
 
     # -- timing

@@ -277,28 +277,68 @@ def test_3d_256x256x128_fp32_two_steps_full_grid():
 
 # ------------------------------------------------------------------ solver forms
 @pytest.mark.parametrize("n,h", [((100, 64), (0.12, 0.15)), ((132, 36), (0.1, 0.3)),
-                                 ((44, 36, 40), (0.3, 0.3, 0.25))])
+                                 ((130, 70), (0.1, 0.12)), ((44, 36, 40), (0.3, 0.3, 0.25)),
+                                 ((70, 50, 46), (0.2, 0.22, 0.25))])
 @pytest.mark.parametrize("imag", [True, False])
-def test_stencil_form_matches_thomas_fp32(n, h, imag):
-    """The banded-inverse stencil and the Thomas solve are the same CN
-    substep: same state after 20 steps up to float rounding."""
+def test_stencil_forms_match_thomas_fp32(n, h, imag):
+    """The fused H1 + x + y tile pass, the separate stencil sweeps and the
+    Thomas solve are the same split step: same state after 20 steps up to
+    float rounding, on grids whose tiles do not divide them."""
     phys = dict(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3)
     R = inputs.random_phase_field(n[0], n[1], 8)
-    a = Solver(n, h, precision="fp32", **phys)
-    b = Solver(n, h, precision="fp32", **phys)
-    info = a.info()
-    assert all(t > 0 for t in info["stencil_taps"]), info
-    for axis in range(len(n)):
-        b.set_solver(axis, "thomas")
-    assert all(t == 0 for t in b.info()["stencil_taps"])
-    for s in (a, b):
+    forms = {}
+    fused = Solver(n, h, precision="fp32", **phys)
+    fused.set_solver(0, "fused")
+    for axis in range(2, len(n)):
+        fused.set_solver(axis, "stencil")
+    info = fused.info()
+    assert info["fused_xy"] == 1 and all(t > 0 for t in info["stencil_taps"]), info
+    forms["fused"] = fused
+    if n[0] % 4 == 0:
+        sep = Solver(n, h, precision="fp32", **phys)
+        for axis in range(len(n)):
+            sep.set_solver(axis, "stencil")
+        assert sep.info()["fused_xy"] == 0
+        forms["stencil"] = sep
+    th = Solver(n, h, precision="fp32", **phys)  # the default form
+    assert all(t == 0 for t in th.info()["stencil_taps"]) and th.info()["fused_xy"] == 0
+    forms["thomas"] = th
+    psi = {}
+    for k, s in forms.items():
         s.init_analytic(1, R, 1.0, 1.0)
         (s.step_imag if imag else s.step_real)(20)
-    pa, pb = a.get_psi(), b.get_psi()
-    # float rounding of two evaluation orders over 20 steps of a rough
-    # random-phase state (the stencil's truncated tail is below 2e-10)
-    assert np.max(np.abs(pa - pb)) <= 5e-6 * np.max(np.abs(pb))
+        psi[k] = s.get_psi()
     grid = Grid(n, h)
     ref, _ = oracle.steps(grid, Phys(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3),
                           oracle.init_analytic(grid, 1, R), 20, imag)
-    assert np.max(np.abs(pa - ref)) <= 5e-6 * np.max(np.abs(ref))
+    # float rounding of different evaluation orders over 20 steps of a rough
+    # random-phase state (the stencil's truncated tail is below 2e-10)
+    scale = np.max(np.abs(ref))
+    for k, p in psi.items():
+        assert np.max(np.abs(p - psi["thomas"])) <= 5e-6 * scale, k
+        assert np.max(np.abs(p - ref)) <= 5e-6 * scale, k
+    # the zero edges stay exactly zero
+    for p in psi.values():
+        for ax in range(len(n)):
+            assert np.all(np.take(p, [0, n[ax]], axis=len(n) - 1 - ax) == 0)
+
+
+def test_fused_pass_selection():
+    """Selecting a per-axis solver turns the fused pass off; FUSED turns it
+    back on; FUSED is refused on z."""
+    s = Solver((64, 48, 32), (0.2, 0.2, 0.25), precision="fp32", gamma=1.0, nu=1.0, lam=1.0,
+               g=50.0, omega=0.5, dt=1e-3)
+    assert s.info()["fused_xy"] == 0
+    s.set_solver(0, "fused")
+    assert s.info()["fused_xy"] == 1
+    s.set_solver(1, "thomas")
+    assert s.info()["fused_xy"] == 0 and s.info()["stencil_taps"][1] == 0
+    s.set_solver(0, "fused")
+    assert s.info()["fused_xy"] == 1 and s.info()["stencil_taps"][1] > 0
+    with pytest.raises(RotgpError):
+        s.set_solver(2, "fused")
+    d = Solver((64, 48), (0.2, 0.2), precision="fp64", gamma=1.0, nu=1.0, g=50.0, omega=0.5,
+               dt=1e-3)
+    assert d.info()["fused_xy"] == 0
+    with pytest.raises(RotgpError):
+        d.set_solver(0, "fused")

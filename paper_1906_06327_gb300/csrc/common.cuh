@@ -106,6 +106,7 @@ struct tile_args {
   int nx, ny, nz;        // stored points per axis
   int bx, by, bz;        // end rows with their own weights, per axis
   int tiles_x, tiles_y;  // xy pass: tiles per plane; line pass: patches across the lines
+  int zchunk;            // xy pass: z planes per CTA
   // H1 substep and the pending scale (xy pass)
   float dt, g, hgam2, hnu2, hlam2;
   float x0, hx, y0, hy, z0, hz;
@@ -175,6 +176,7 @@ inline bool stencil_k_built(int K) { return K == 4 || K == 6 || K == 8; }
 // launch_* return cudaErrorInvalidValue for an unbuilt K (tile_k_built).
 bool tile_k_built(int K);
 unsigned xy_pass_smem(int K);  // dynamic shared memory of one xy-pass CTA
+int xy_pass_ctas_per_sm(int K, bool imag, bool reduce);  // resident CTAs per SM
 void xy_tile_geometry(int K, int* TX, int* TY, int* R, int* WX);
 int line_rows();
 cudaError_t launch_xy_pass(bool imag, bool reduce, int K, const void* map, const tile_args& a,

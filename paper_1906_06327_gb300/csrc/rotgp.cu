@@ -370,15 +370,27 @@ int plan_axes(rotgp_ctx* c) {
   return ROTGP_OK;
 }
 
-// blocks of the tile passes: the xy pass is persistent, as many CTAs as fit
-// on the SMs (at most one per tile)
-unsigned xy_blocks(const rotgp_ctx* c) {
+// Launch shape of the xy pass: one CTA per (tile, range of z planes), the
+// ranges as long as one wave of resident CTAs allows (2D: one CTA per tile).
+void xy_shape(const rotgp_ctx* c, int* tiles_x, int* tiles_y, int* zchunk, unsigned* blocks) {
   int TX, TY, R, WX;
-  xy_tile_geometry(c->axis[0].sK, &TX, &TY, &R, &WX);
-  const long long tiles = (long long)((c->nx + TX - 1) / TX) * ((c->ny + TY - 1) / TY) * c->nz;
-  const long long per_sm = std::max<long long>(
-      1, std::min<long long>(8, (228 * 1024) / (xy_pass_smem(c->axis[0].sK) + 2048)));
-  return (unsigned)std::min<long long>(tiles, per_sm * c->sm_count);
+  const int K = c->axis[0].sK;
+  xy_tile_geometry(K, &TX, &TY, &R, &WX);
+  *tiles_x = (c->nx + TX - 1) / TX;
+  *tiles_y = (c->ny + TY - 1) / TY;
+  const long long txy = (long long)*tiles_x * *tiles_y;
+  // occupancy of the most demanding instantiation (real time, with norm)
+  const long long resident =
+      (long long)xy_pass_ctas_per_sm(K, false, c->grid.dim == 2) * c->sm_count;
+  const int chunks = (int)std::max<long long>(1, std::min<long long>(c->nz, resident / txy));
+  *zchunk = (c->nz + chunks - 1) / chunks;
+  *blocks = (unsigned)(txy * ((c->nz + *zchunk - 1) / *zchunk));
+}
+unsigned xy_blocks(const rotgp_ctx* c) {
+  int tx, ty, zc;
+  unsigned b;
+  xy_shape(c, &tx, &ty, &zc, &b);
+  return b;
 }
 unsigned line_blocks(const rotgp_ctx* c, int axis) {
   const int nt = axis == 1 ? c->nz : c->ny, rows = line_rows();
@@ -518,14 +530,12 @@ tile_args make_tile_args(rotgp_ctx* c, bool imag) {
 // H1, x and y sweeps in one pass (the whole step in 2D)
 int xy_pass(rotgp_ctx* c, bool imag) {
   tile_args t = make_tile_args(c, imag);
-  int TX, TY, R, WX;
-  xy_tile_geometry(c->axis[0].sK, &TX, &TY, &R, &WX);
-  t.tiles_x = (c->nx + TX - 1) / TX;
-  t.tiles_y = (c->ny + TY - 1) / TY;
+  unsigned blocks;
+  xy_shape(c, &t.tiles_x, &t.tiles_y, &t.zchunk, &blocks);
   cudaError_t e;
   {
     Timed tm(c, K_XY);
-    e = launch_xy_pass(imag, c->grid.dim == 2, c->axis[0].sK, &c->map_xy[c->cur], t, xy_blocks(c),
+    e = launch_xy_pass(imag, c->grid.dim == 2, c->axis[0].sK, &c->map_xy[c->cur], t, blocks,
                        c->stream);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "xy pass launch");

@@ -11,8 +11,9 @@
 // are done with it, so up to seven boxes per CTA are in flight.  A warp's
 // 32 lanes are the 32 x values of one transverse row: every shared-memory
 // read and global store of a warp is 256 contiguous bytes.  Each thread
-// keeps the last 2K + 1 positions of its line in a register window; an
-// output is produced as soon as its last neighbour has landed.  In 3D the z
+// carries the last 2K positions of its line in registers from box to box
+// and produces a box's eight outputs together (sixteen independent FMA
+// chains; boxes at a line end take per-position weights).  In 3D the z
 // sweep is the last of the step and also reduces the norm.
 #include "sweep_common.cuh"
 #include "tma.cuh"
@@ -68,44 +69,61 @@ __global__ void __launch_bounds__(64) k_line_pass(const __grid_constant__ CUtens
                 (AX == 2 ? (size_t)t2 * a.nx : (size_t)t2 * a.ny * a.nx);
   const size_t ostep = AX == 2 ? (size_t)a.ny * a.nx : (size_t)a.nx;
   acc_t<float> acc;
-  // win[t] holds staged position p - 2K + t once position p is loaded
-  float2 win[S];
+  // win[t]: staged positions 8b - 2K + t (t < 2K) before box b is read;
+  // u[]: those followed by the box's 8 positions, so that output j of the
+  // box (position 8b - 2K + j) uses u[j .. j + 2K]
+  float2 win[2 * K];
 #pragma unroll
-  for (int t = 0; t < S; ++t) win[t] = make_float2(0.f, 0.f);
+  for (int t = 0; t < 2 * K; ++t) win[t] = make_float2(0.f, 0.f);
   bool good = true;
   int b = 0;
   for (; b < nb; ++b) {
     const int slot = b % kSlots;
     good = mbar_wait(&full[slot], (b / kSlots) & 1);
     const float2* sl = ring + slot * kSlot;
+    float2 u[2 * K + kBox];
 #pragma unroll
-    for (int j = 0; j < kBox; ++j) {
-      const int p = kBox * b + j;
+    for (int t = 0; t < 2 * K; ++t) u[t] = win[t];
 #pragma unroll
-      for (int t = 0; t < 2 * K; ++t) win[t] = win[t + 1];
-      win[2 * K] = sl[(AX == 2 ? j * kRows + w : w * kBox + j) * 32 + lane];
-      const int s = p - 2 * K;  // output position, with neighbours s-K .. s+K loaded
-      if (s >= 0 && s < N) {
+    for (int j = 0; j < kBox; ++j)
+      u[2 * K + j] = sl[(AX == 2 ? j * kRows + w : w * kBox + j) * 32 + lane];
+    const int s0 = kBox * b - 2 * K;  // output position of j = 0
+    float2 r[kBox];
+    if (s0 >= B && s0 + kBox <= N - B) {
+      // interior box: eight independent outputs, no branches
+#pragma unroll
+      for (int j = 0; j < kBox; ++j) {
         cacc c = cacc_zero();
-        if (s >= B && s < N - B) {
 #pragma unroll
-          for (int t = 0; t < S; ++t) cmac(c, WR[t], WI[t], win[t]);
-        } else {
-          const float2* wr = wl + stencil_row(s, N, B) * S;
+        for (int t = 0; t < S; ++t) cmac(c, WR[t], WI[t], u[j + t]);
+        r[j] = cfin(c);
+      }
+    } else {
+      // a line end (or the ramp-up before the first output): per-output rows
 #pragma unroll
-          for (int t = 0; t < S; ++t) {
-            float2 pr, pi;
-            wsplit(wr[t], pr, pi);
-            cmac(c, pr, pi, win[t]);
-          }
+      for (int j = 0; j < kBox; ++j) {
+        const int s = s0 + j;
+        const float2* wr = wl + stencil_row(min(max(s, 0), N - 1), N, B) * S;
+        cacc c = cacc_zero();
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          float2 pr, pi;
+          wsplit(wr[t], pr, pi);
+          cmac(c, pr, pi, u[j + t]);
         }
-        const float2 r = cfin(c);
-        if (store_ok) {
-          out[(size_t)s * ostep] = r;
-          if (REDUCE) acc.add(fmaf(r.x, r.x, r.y * r.y));
-        }
+        r[j] = cfin(c);
       }
     }
+#pragma unroll
+    for (int j = 0; j < kBox; ++j) {
+      const int s = s0 + j;
+      if (store_ok && s >= 0 && s < N) {
+        out[(size_t)s * ostep] = r[j];
+        if (REDUCE) acc.add(fmaf(r[j].x, r[j].x, r[j].y * r[j].y));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2 * K; ++t) win[t] = u[kBox + t];
     // both warps are done with this slot: refill it
     if (!__syncthreads_and(good)) break;
     if (tid == 0 && b + kSlots < nb) issue(b + kSlots);

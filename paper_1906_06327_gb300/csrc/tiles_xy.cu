@@ -15,18 +15,20 @@
 //      CTAs are persistent (a few per SM, tiles taken round-robin) and
 //      double-buffer the tiles: the next tile's load is in flight while the
 //      current one is computed;
-//   2. the pending renormalisation and H1 (Eq. eq1) are applied once per
-//      point, in place;
-//   3. the x stencil runs on all TY + 2K rows (the halo rows are needed by
-//      the y stencil), one row per lane, four outputs per step;
-//   4. the y stencil runs down the TX columns of the TY output rows, M
+//   2. the x stencil runs on all TY + 2K rows (the halo rows are needed by
+//      the y stencil): a lane owns one row and a warp a strip of 16
+//      outputs; the lane reads its 16 + 2K window, applies the pending
+//      renormalisation and H1 (Eq. eq1) to it in registers (neighbouring
+//      strips recompute the 2K halo points), and writes 16 outputs;
+//   3. the y stencil runs down the TX columns of the TY output rows, M
 //      outputs per thread from a register window, and the result is stored
 //      to the other state buffer.  In 2D this completes the step and the
 //      block also reduces the norm of what it stored.
 //
-// The halo points are recomputed by neighbouring tiles (H1 on (TY+2K) x
-// (TX+2K') points and the x stencil on TY + 2K rows per TY output rows); in
-// exchange the state crosses HBM once per pass instead of once per sweep.
+// The halo points are recomputed by neighbouring tiles and strips (H1 on
+// (TY + 2K) x 4 (16 + 2K) points and the x stencil on TY + 2K rows per
+// TX x TY outputs); in exchange the state crosses HBM once per pass instead
+// of once per sweep.
 #include "sweep_common.cuh"
 #include "tma.cuh"
 
@@ -46,183 +48,189 @@ struct xy_geom {
   static_assert(R <= 32 && TY % 4 == 0 && WX % 2 == 0 && BYTES % 128 == 0, "tile geometry");
 };
 
-// pending scale and H1 on two adjacent points (re, im, re, im); va, vb are
-// their trap potentials
+// pending scale and H1 on one point held in registers; vxyz is its trap
+// potential
 template <bool IMAG>
-__device__ __forceinline__ float4 h1_pair(float4 v, float s, float va, float vb, float g,
-                                          float dt) {
+__device__ __forceinline__ float2 h1_point(float2 v, float s, float vxyz, float g, float dt) {
   v.x *= s;
   v.y *= s;
-  v.z *= s;
-  v.w *= s;
-  const float ea = fmaf(g, fmaf(v.x, v.x, v.y * v.y), va);
-  const float eb = fmaf(g, fmaf(v.z, v.z, v.w * v.w), vb);
+  const float e = fmaf(g, fmaf(v.x, v.x, v.y * v.y), vxyz);
   if (IMAG) {
-    const float fa = __expf(-dt * ea), fb = __expf(-dt * eb);
-    return make_float4(fa * v.x, fa * v.y, fb * v.z, fb * v.w);
+    const float f = __expf(-dt * e);
+    return make_float2(f * v.x, f * v.y);
   } else {
-    float sa, ca, sb, cb;
-    sincosf(dt * ea, &sa, &ca);
-    sincosf(dt * eb, &sb, &cb);
-    return make_float4(fmaf(ca, v.x, sa * v.y), fmaf(ca, v.y, -sa * v.x), fmaf(cb, v.z, sb * v.w),
-                       fmaf(cb, v.w, -sb * v.z));
+    float sn, cs;
+    sincosf(dt * e, &sn, &cs);
+    return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
   }
 }
 
-// one output of a stencil with table weights w (2K+1 taps) over inputs in[0..2K]
-template <int K>
-__device__ __forceinline__ float2 stencil_slow(const float2* w, const float2* in, int step) {
-  cacc c = cacc_zero();
-#pragma unroll 1
-  for (int t = 0; t <= 2 * K; ++t) {
-    float2 wr, wi;
-    wsplit(w[t], wr, wi);
-    cmac(c, wr, wi, in[t * step]);
-  }
-  return cfin(c);
-}
-
+// One CTA per (x-y tile, range of z planes): the tile position is fixed, so
+// each lane's x weights (its row) stay in registers for the whole range, and
+// so do its y weights (its column) when K = 4 (longer stencils reload them
+// per plane from L1: both sets would not fit).  Planes are double-buffered:
+// the TMA load of the next plane is in flight while the current one is
+// computed.
 template <int K, bool IMAG, bool REDUCE>
 __global__ void __launch_bounds__(128) k_xy_pass(const __grid_constant__ CUtensorMap map,
                                                  const tile_args a) {
   using G = xy_geom<K>;
   constexpr int S = 2 * K + 1;
-  // dynamic shared memory: two staged tiles, then the x-stage output
+  constexpr int XS = 16;          // x outputs of one warp's strip
+  constexpr int NWIN = XS + 2 * K;
+  static_assert(G::KP == K, "x halo must start on a 16-byte boundary");
   extern __shared__ __align__(128) unsigned char dsm[];
   unsigned char* base = dsm + ((128 - (smem_addr(dsm) & 127)) & 127);
   auto raw = [&](int bf) { return reinterpret_cast<float2*>(base + bf * G::BYTES); };
   float2* xo = reinterpret_cast<float2*>(base + 2 * G::BYTES);
   __shared__ __align__(8) uint64_t bar[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per_plane = a.tiles_x * a.tiles_y;
-  const int ntiles = per_plane * a.nz;
+  const int tiles_xy = a.tiles_x * a.tiles_y;
+  const int txy = blockIdx.x % tiles_xy;
+  const int zb = (blockIdx.x / tiles_xy) * a.zchunk;
+  const int ze = min(a.nz, zb + a.zchunk);
+  const int x0 = (txy % a.tiles_x) * G::TX, y0 = (txy / a.tiles_x) * G::TY;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  // thread 0: start the TMA load of tile t into buffer bf
-  auto issue = [&](int t, int bf) {
-    const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, z = t / per_plane;
+  auto issue = [&](int z, int bf) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&bar[bf], G::BYTES);
-    tma_load_3d(raw(bf), &map, 2 * (tx * G::TX - G::KP), ty * G::TY - K, z, &bar[bf]);
+    tma_load_3d(raw(bf), &map, 2 * (x0 - K), y0 - K, z, &bar[bf]);
   };
-  int t = blockIdx.x;
-  if (tid == 0 && t < ntiles) issue(t, 0);
+  if (tid == 0 && zb < ze) issue(zb, 0);
+  // x stage: lane = tile row r, warp = strip of 16 outputs
+  const int r = lane;
+  const float2* wxl = static_cast<const float2*>(a.wx) +
+                      (size_t)min(max(y0 - K + r, 0), a.ny - 1) * (2 * a.bx + 1) * S;
+  float2 XR[S], XI[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) wsplit(wxl[a.bx * S + t], XR[t], XI[t]);
+  const int xq0 = x0 + XS * warp;  // first output of the strip
+  const bool x_fast = xq0 >= a.bx && xq0 + XS - 1 < a.nx - a.bx;
+  const float yc = a.y0 + (float)(y0 - K + r) * a.hy;
+  const float vy = a.hnu2 * yc * yc;
+  const float xw = a.x0 + (float)(xq0 - K) * a.hx;  // x of window point 0
+  // y stage: lane = column (two column halves), groups of M rows
+  const int cx = 32 * (warp & 1) + lane;
+  const int x = x0 + cx;
+  const float2* wyl =
+      static_cast<const float2*>(a.wy) + (size_t)min(x, a.nx - 1) * (2 * a.by + 1) * S;
+  constexpr bool YREG = K <= 4;
+  float2 YR[YREG ? S : 1], YI[YREG ? S : 1];
+  if (YREG) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) wsplit(wyl[a.by * S + t], YR[t], YI[t]);
+  }
+  const float sc = (float)(*a.scale);
   acc_t<float> acc;
   bool good = true;
   int k = 0;
-  for (; t < ntiles; ++k, t += gridDim.x) {
+  for (int z = zb; z < ze; ++k, ++z) {
     const int bf = k & 1;
-    // prefetch the next tile into the other buffer: its last reader (the x
-    // stage of the previous tile) finished before the previous barrier
-    if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x, bf ^ 1);
-    const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, z = t / per_plane;
-    const int x0 = tx * G::TX, y0 = ty * G::TY;
-    // x weights of this lane's row (interior row), while the tile lands
-    const int r = lane;
-    const int jx = min(max(y0 - K + r, 0), a.ny - 1);
-    const float2* wxl = static_cast<const float2*>(a.wx) + (size_t)jx * (2 * a.bx + 1) * S;
-    float2 WR[S], WI[S];
-#pragma unroll
-    for (int q = 0; q < S; ++q) wsplit(wxl[a.bx * S + q], WR[q], WI[q]);
+    // the other buffer's last reader (the x stage of the previous plane)
+    // finished before the previous barrier
+    if (tid == 0 && z + 1 < ze) issue(z + 1, bf ^ 1);
     if (!__syncthreads_and(mbar_wait(&bar[bf], (k >> 1) & 1))) {
       good = false;
       break;
     }
-    float2* tile = raw(bf);
-    // ---- 2. pending scale and H1, in place
-    {
-      const float s = (float)(*a.scale);
-      const float zc = a.z0 + (float)z * a.hz;
-      const float vz = a.hlam2 * zc * zc;
-      constexpr int HALF = G::WX / 2;
-      for (int u = tid; u < G::R * HALF; u += 128) {
-        const int rr = u / HALF;
-        const int i = 2 * (u - rr * HALF);
-        float4* p = reinterpret_cast<float4*>(tile + rr * G::WX + i);
-        const float yc = a.y0 + (float)(y0 - K + rr) * a.hy;
-        const float xa = a.x0 + (float)(x0 - G::KP + i) * a.hx;
-        const float xb = xa + a.hx;
-        const float vyz = fmaf(a.hnu2, yc * yc, vz);
-        *p = h1_pair<IMAG>(*p, s, fmaf(a.hgam2, xa * xa, vyz), fmaf(a.hgam2, xb * xb, vyz), a.g,
-                           a.dt);
-      }
-    }
-    __syncthreads();
-    // ---- 3. x stencil on every loaded row: lane = row, warp = quads of 4 outputs
+    // ---- x stage with the pending scale and H1 applied to the window
     if (r < G::R) {
-      constexpr int NW = (4 + 2 * G::KP) / 2;  // float4 of the window
-      constexpr int OFF = G::KP - K;
-      const float2* row = tile + r * G::WX;
-      float2* orow = xo + r * G::PX;
-      for (int q = warp; q < G::TX / 4; q += 4) {
-        const int xq = x0 + 4 * q;
-        float2 o[4];
-        if (xq >= a.bx && xq + 3 < a.nx - a.bx) {
-          const float4* src = reinterpret_cast<const float4*>(row + 4 * q);
-          float4 wv[NW];
+      const float zc = a.z0 + (float)z * a.hz;
+      const float vyz = fmaf(a.hlam2, zc * zc, vy);
+      const float4* src = reinterpret_cast<const float4*>(raw(bf) + r * G::WX + XS * warp);
+      float2 v[NWIN];
 #pragma unroll
-          for (int i = 0; i < NW; ++i) wv[i] = src[i];
+      for (int i = 0; i < NWIN / 2; ++i) {
+        const float4 q = src[i];
+        v[2 * i] = make_float2(q.x, q.y);
+        v[2 * i + 1] = make_float2(q.z, q.w);
+      }
 #pragma unroll
-          for (int m = 0; m < 4; ++m) {
+      for (int t = 0; t < NWIN; ++t) {
+        const float xc = fmaf((float)t, a.hx, xw);
+        v[t] = h1_point<IMAG>(v[t], sc, fmaf(a.hgam2, xc * xc, vyz), a.g, a.dt);
+      }
+      float4* dst = reinterpret_cast<float4*>(xo + r * G::PX + XS * warp);
+      if (x_fast) {
+#pragma unroll
+        for (int m = 0; m < XS; m += 2) {
+          cacc c0 = cacc_zero(), c1 = cacc_zero();
+#pragma unroll
+          for (int t = 0; t < S; ++t) {
+            cmac(c0, XR[t], XI[t], v[m + t]);
+            cmac(c1, XR[t], XI[t], v[m + 1 + t]);
+          }
+          const float2 o0 = cfin(c0), o1 = cfin(c1);
+          dst[m / 2] = make_float4(o0.x, o0.y, o1.x, o1.y);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < XS; m += 2) {
+          float2 o[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int xo_ = xq0 + m + e;
+            const float2* wr = wxl + stencil_row(min(xo_, a.nx - 1), a.nx, a.bx) * S;
             cacc c = cacc_zero();
 #pragma unroll
-            for (int j = 0; j < S; ++j) {
-              const int i = OFF + m + j;
-              const float4 w4 = wv[i >> 1];
-              cmac(c, WR[j], WI[j], (i & 1) ? make_float2(w4.z, w4.w) : make_float2(w4.x, w4.y));
+            for (int t = 0; t < S; ++t) {
+              float2 pr, pi;
+              wsplit(wr[t], pr, pi);
+              cmac(c, pr, pi, v[m + e + t]);
             }
-            o[m] = cfin(c);
+            o[e] = xo_ < a.nx ? cfin(c) : make_float2(0.f, 0.f);
           }
-        } else {
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            const int x = xq + m;
-            o[m] = make_float2(0.f, 0.f);
-            if (x < a.nx)
-              o[m] = stencil_slow<K>(wxl + stencil_row(x, a.nx, a.bx) * S, row + 4 * q + OFF + m, 1);
-          }
+          dst[m / 2] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
         }
-        float4* dst = reinterpret_cast<float4*>(orow + 4 * q);
-        dst[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-        dst[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
       }
     }
     __syncthreads();
-    // ---- 4. y stencil: lane = column (two column halves), M rows per group
+    // ---- y stage
     {
-      const int cx = 32 * (warp & 1) + lane;
-      const int x = x0 + cx;
-      const float2* wyl =
-          static_cast<const float2*>(a.wy) + (size_t)min(x, a.nx - 1) * (2 * a.by + 1) * S;
-#pragma unroll
-      for (int q = 0; q < S; ++q) wsplit(wyl[a.by * S + q], WR[q], WI[q]);
       float2* out = static_cast<float2*>(a.out) + (size_t)z * a.ny * a.nx + x;
       for (int gq = warp >> 1; gq < 4; gq += 2) {
         const int yg = y0 + gq * G::M;
         const float2* col = xo + gq * G::M * G::PX + cx;
+        float2 win[G::M + 2 * K];
+#pragma unroll
+        for (int i = 0; i < G::M + 2 * K; ++i) win[i] = col[i * G::PX];
         float2 o[G::M];
         if (yg >= a.by && yg + G::M - 1 < a.ny - a.by) {
-          float2 win[G::M + 2 * K];
+          float2 QR[S], QI[S];
 #pragma unroll
-          for (int i = 0; i < G::M + 2 * K; ++i) win[i] = col[i * G::PX];
+          for (int t = 0; t < S; ++t) {
+            if (YREG) {
+              QR[t] = YR[YREG ? t : 0];
+              QI[t] = YI[YREG ? t : 0];
+            } else {
+              wsplit(wyl[a.by * S + t], QR[t], QI[t]);
+            }
+          }
 #pragma unroll
           for (int m = 0; m < G::M; ++m) {
             cacc c = cacc_zero();
 #pragma unroll
-            for (int j = 0; j < S; ++j) cmac(c, WR[j], WI[j], win[m + j]);
+            for (int t = 0; t < S; ++t) cmac(c, QR[t], QI[t], win[m + t]);
             o[m] = cfin(c);
           }
         } else {
 #pragma unroll
           for (int m = 0; m < G::M; ++m) {
             const int y = yg + m;
-            o[m] = make_float2(0.f, 0.f);
-            if (y < a.ny)
-              o[m] = stencil_slow<K>(wyl + stencil_row(y, a.ny, a.by) * S, col + m * G::PX, G::PX);
+            const float2* wr = wyl + stencil_row(min(y, a.ny - 1), a.ny, a.by) * S;
+            cacc c = cacc_zero();
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+              float2 pr, pi;
+              wsplit(wr[t], pr, pi);
+              cmac(c, pr, pi, win[m + t]);
+            }
+            o[m] = cfin(c);
           }
         }
         if (x < a.nx) {
@@ -237,12 +245,12 @@ __global__ void __launch_bounds__(128) k_xy_pass(const __grid_constant__ CUtenso
         }
       }
     }
-    // the next iteration's first barrier orders these reads of xo before
-    // the next x stage writes it
+    // the next plane's first barrier orders these reads of xo before the
+    // next x stage writes it
   }
   if (!good) {
     // let the prefetch in flight (if any) land before the CTA leaves
-    if (t + (int)gridDim.x < ntiles) mbar_wait(&bar[(k & 1) ^ 1], ((k + 1) >> 1) & 1);
+    if (zb + k + 1 < ze) mbar_wait(&bar[(k & 1) ^ 1], ((k + 1) >> 1) & 1);
     if (tid == 0) atomicOr(a.flags, 4);
   }
   if (REDUCE) norm_epilogue(acc.value(), a);
@@ -258,13 +266,45 @@ void xy_tile_geometry(int K, int* TX, int* TY, int* R, int* WX) {
   *WX = 64 + 2 * KP + 2;
 }
 
+// opt an instantiation in to its dynamic shared memory, once
+template <int K, bool IMAG, bool REDUCE>
+cudaError_t xy_allow_smem() {
+  static const cudaError_t e = cudaFuncSetAttribute(
+      k_xy_pass<K, IMAG, REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)xy_geom<K>::SMEM);
+  return e;
+}
+
+template <int K, bool IMAG, bool REDUCE>
+int xy_ctas_k() {
+  int n = 0;
+  if (xy_allow_smem<K, IMAG, REDUCE>() != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_xy_pass<K, IMAG, REDUCE>, 128,
+                                                    xy_geom<K>::SMEM) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+int xy_pass_ctas_per_sm(int K, bool imag, bool reduce) {
+#define ROTGP_XO(KK)                                                     \
+  if (K == KK) {                                                         \
+    if (imag && reduce) return xy_ctas_k<KK, true, true>();              \
+    if (imag) return xy_ctas_k<KK, true, false>();                       \
+    if (reduce) return xy_ctas_k<KK, false, true>();                     \
+    return xy_ctas_k<KK, false, false>();                                \
+  }
+  ROTGP_XO(4)
+  ROTGP_XO(6)
+  ROTGP_XO(8)
+#undef ROTGP_XO
+  return 1;
+}
+
 template <int K, bool IMAG, bool REDUCE>
 cudaError_t launch_xy_k(const CUtensorMap& m, const tile_args& a, unsigned blocks,
                         cudaStream_t s) {
   using G = xy_geom<K>;
-  // opt this instantiation in to its dynamic shared memory, once
-  static const cudaError_t e = cudaFuncSetAttribute(
-      k_xy_pass<K, IMAG, REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+  const cudaError_t e = xy_allow_smem<K, IMAG, REDUCE>();
   if (e != cudaSuccess) return e;
   k_xy_pass<K, IMAG, REDUCE><<<blocks, 128, G::SMEM, s>>>(m, a);
   return cudaGetLastError();

@@ -43,6 +43,11 @@ def _args():
     p.add_argument("--skip-baselines", action="store_true",
                    help="no e2e and no CPU baseline (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="keep the default solver forms instead of timing the candidates")
+    p.add_argument("--forms", default="",
+                   help="solver form per axis, e.g. thomas,thomas,stencil (skips the autotuner;"
+                        " used to profile the forms a timed run chose)")
     return p.parse_args()
 
 
@@ -207,6 +212,21 @@ def run_ours(a, w):
                precision=precision, stream=stream.cuda_stream)
     R = inputs.random_phase_field(w.n[0], w.n[1], w.seed + rank)
     s.init_analytic(1, R, 1.0, 1.0)
+    # solver forms picked by timing them on this grid (untimed setup, like a plan)
+    if a.forms:
+        forms = a.forms.split(",")
+        if len(forms) != len(w.n) or not set(forms) <= {"thomas", "stencil", "fused"}:
+            raise SystemExit("--forms: one of thomas/stencil/fused per axis")
+        for ax, f in enumerate(forms):
+            if f != "fused":
+                s.set_solver(ax, f)
+        if "fused" in forms:
+            s.set_solver(0, "fused")
+        tuned = {"choice": -1, "forms": forms}
+    elif a.autotune:
+        tuned = s.autotune(steps=3)
+    else:
+        tuned = {"choice": 0, "forms": ["thomas"] * len(w.n)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def bench_step():
@@ -309,6 +329,7 @@ def run_ours(a, w):
                              f"{w.sites * (16 if precision == 'fp64' else 8) / 2**20:.0f} MiB "
                              "state can stay L2-resident within a step",
                        "parallelism": f"replicas x{world}",
+                       "solver_forms": tuned["forms"],
                        "solver": s.info()},
             "gpu_launches": launches,
             "roofline": roofline,

@@ -203,6 +203,18 @@ int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring
 #define ROTGP_SOLVER_FUSED 2
 int rotgp_set_solver(rotgp_ctx* ctx, int axis, int solver);
 
+/* Pick the fastest line-solver forms for this context by timing them.
+ * Candidates: every combination of ROTGP_SOLVER_THOMAS / ROTGP_SOLVER_STENCIL
+ * per axis that the context supports, and the fused x-y pass with each form
+ * of the z sweep.  Each candidate runs one warm-up and then `steps`
+ * imaginary-time steps from a copy of the current state, timed with CUDA
+ * events on the context's stream; the state, its pending renormalisation
+ * and the step counter are restored afterwards, and the fastest candidate
+ * stays selected.  *choice (if not NULL) receives it as a bit set: bit a =
+ * axis a in stencil form, bit 3 = fused x-y pass.  Synchronises the stream.
+ * ROTGP_EINVAL if steps < 1. */
+int rotgp_autotune(rotgp_ctx* ctx, int steps, int* choice);
+
 /* Per-kernel CUDA-event timing.  While enabled, every kernel launch of the
  * context is bracketed by events on its stream.  rotgp_profile_read
  * synchronises, fills up to max records (one per kernel name), sets *count

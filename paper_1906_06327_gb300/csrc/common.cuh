@@ -107,6 +107,7 @@ struct tile_args {
   int bx, by, bz;        // end rows with their own weights, per axis
   int tiles_x, tiles_y;  // xy pass: tiles per plane; line pass: patches across the lines
   int zchunk;            // xy pass: z planes per CTA
+  int seg_len;           // line pass: outputs per line segment
   // H1 substep and the pending scale (xy pass)
   float dt, g, hgam2, hnu2, hlam2;
   float x0, hx, y0, hy, z0, hz;

@@ -2,6 +2,7 @@
 // lifetime, solver sizing, launch plans of one split step (Sec. 2: H1 fused
 // into the x sweep, then the y sweep and, in 3D, the z sweep, with the norm
 // reduced in the last sweep), observables, state I/O and kernel timing.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -48,6 +49,7 @@ struct AxisPlan {
   bool stencil_ok = false;  // stencil form available for this axis
   bool use_stencil = false;
   int sK = 0, sB = 0;
+  int lsegs = 1;  // segments per line of the stencil line pass (y, z)
   void* wtab[2] = {nullptr, nullptr};
 };
 
@@ -351,6 +353,14 @@ int plan_axes(rotgp_ctx* c) {
     if (ap.stencil_ok) {
       ap.sK = K;
       ap.sB = B;
+      if (!x) {
+        // line pass: enough segments for ~24 resident warps per SM, each
+        // segment at least 16 points
+        const long long nt = a == 1 ? c->nz : c->ny;
+        const long long warps = ((c->nx + 31) / 32) * ((nt + 1) / 2) * 2;
+        const long long want = (24LL * c->sm_count + warps - 1) / warps;
+        ap.lsegs = (int)std::max(1LL, std::min(want, (long long)std::min(8, ap.len / 16)));
+      }
     }
     // default: the Thomas form (the stencil and fused forms are selected by
     // rotgp_set_solver or rotgp_autotune)
@@ -392,10 +402,18 @@ unsigned xy_blocks(const rotgp_ctx* c) {
   xy_shape(c, &tx, &ty, &zc, &b);
   return b;
 }
+// line pass: patches of 32 x line_rows() lines times segments per line
+int line_seg_len(const rotgp_ctx* c, int axis) {
+  const AxisPlan& ap = c->axis[axis];
+  return (ap.len + ap.lsegs - 1) / ap.lsegs;
+}
 unsigned line_blocks(const rotgp_ctx* c, int axis) {
   const int nt = axis == 1 ? c->nz : c->ny, rows = line_rows();
-  return (unsigned)(((c->nx + 31) / 32) * ((nt + rows - 1) / rows));
+  const int L = line_seg_len(c, axis);
+  return (unsigned)(((c->nx + 31) / 32) * ((nt + rows - 1) / rows) *
+                    ((c->axis[axis].len + L - 1) / L));
 }
+constexpr int kMaxLineSegs = 8;
 
 // Driver entry point of the tensor-map encoder, looked up once.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -601,6 +619,7 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
       tile_args ta = make_tile_args(c, imag);
       ta.tiles_x = (c->nx + 31) / 32;
       ta.tiles_y = ((axis == 1 ? c->nz : c->ny) + line_rows() - 1) / line_rows();
+      ta.seg_len = line_seg_len(c, axis);
       e = launch_line_pass(axis, last, ap.sK, axis == 1 ? &c->map_y[c->cur] : &c->map_z[c->cur],
                            ta, line_blocks(c, axis), c->stream);
     } else {
@@ -773,6 +792,8 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
   c->partial_doubles = pd;
   c->staging_bytes = (size_t)(grid->n[0] + 1) * (grid->n[1] + 1) *
                      (grid->dim == 3 ? grid->n[2] + 1 : 1) * 16;
+  // (also the autotuner's copy of the state and its pending scale)
+  c->staging_bytes = std::max(c->staging_bytes, (size_t)pts * (c->fp64 ? 16 : 8) + 64);
   const size_t state = (size_t)c->sites * c->elem;
   const size_t tab_elem = c->fp64 ? sizeof(coef5<double>) : sizeof(coef5<float>);
   rc = dev_alloc(c, &c->psi[0], state);
@@ -793,8 +814,12 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     if (c->fuse_ok && grid->dim == 2)
       c->partial_doubles = std::max(c->partial_doubles, (size_t)xy_blocks(c));
     const int la = grid->dim - 1;
-    if (c->axis[la].stencil_ok && tile_k_built(c->axis[la].sK))
+    if (c->axis[la].stencil_ok && tile_k_built(c->axis[la].sK)) {
+      const int keep = c->axis[la].lsegs;
+      c->axis[la].lsegs = kMaxLineSegs;
       c->partial_doubles = std::max(c->partial_doubles, (size_t)line_blocks(c, la));
+      c->axis[la].lsegs = keep;
+    }
   }
   if (!rc) rc = dev_alloc(c, (void**)&c->partials, c->partial_doubles * sizeof(double));
   if (!rc) rc = dev_alloc(c, (void**)&c->counter, sizeof(unsigned));
@@ -1068,7 +1093,8 @@ int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
   for (int a = 0; a < 3; ++a) {
     const bool on = a < c->grid.dim;
     out->chunk[a] = on ? c->axis[a].sh.C : 0;
-    out->segments[a] = on ? c->axis[a].nseg : 0;
+    out->segments[a] =
+        on ? (a >= 1 && c->axis[a].use_stencil ? c->axis[a].lsegs : c->axis[a].nseg) : 0;
     out->lines_per_lane[a] = on ? c->axis[a].sh.V : 0;
     out->ring[a] = on ? c->axis[a].sh.R : 0;
     out->stencil_taps[a] = on && c->axis[a].use_stencil ? 2 * c->axis[a].sK + 1 : 0;
@@ -1084,6 +1110,14 @@ int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
 int rotgp_tune(rotgp_ctx* c, int axis, int lines_per_lane, int chunk, int ring,
                int warps_per_block, int segments) {
   if (!c) return ROTGP_EINVAL;
+  if (axis >= 1 && axis < c->grid.dim && c->axis[axis].use_stencil) {
+    // stencil form of a y or z sweep: only the segment count applies
+    if (segments < 1 || segments > kMaxLineSegs || segments > c->axis[axis].len / 8)
+      return fail(c, ROTGP_EINVAL, "segments must be 1..%d and leave >= 8 points each",
+                  kMaxLineSegs);
+    c->axis[axis].lsegs = segments;
+    return ROTGP_OK;
+  }
   if (axis < 0 || axis >= c->grid.dim) return fail(c, ROTGP_EINVAL, "axis out of range");
   if (warps_per_block < 1 || warps_per_block > 8)
     return fail(c, ROTGP_EINVAL, "warps_per_block must be 1..8");
@@ -1117,6 +1151,110 @@ int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
   ap.use_stencil = solver == ROTGP_SOLVER_STENCIL;
   if (axis <= 1) c->fuse_xy = false;
   return ROTGP_OK;
+}
+
+int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
+  if (!c) return ROTGP_EINVAL;
+  if (steps < 1) return fail(c, ROTGP_EINVAL, "steps must be >= 1");
+  const int dim = c->grid.dim;
+  // candidate forms: bit a = axis a in stencil form, bit 3 = fused x-y pass
+  std::vector<int> cand;
+  for (int m = 0; m < (1 << dim); ++m) {
+    bool ok = true;
+    for (int a = 0; a < dim; ++a)
+      if ((m >> a) & 1) ok = ok && c->axis[a].stencil_ok && (a != 0 || c->nx % 4 == 0);
+    if (ok) cand.push_back(m);
+  }
+  if (c->fuse_ok) {
+    cand.push_back(8 | 3);
+    if (dim == 3 && c->axis[2].stencil_ok) cand.push_back(8 | 7);
+  }
+  auto apply = [&](int m) {
+    c->fuse_xy = (m & 8) != 0;
+    for (int a = 0; a < dim; ++a) c->axis[a].use_stencil = ((m >> a) & 1) != 0;
+  };
+  // save the state, its pending scale and the counters
+  const size_t state = (size_t)c->sites * c->elem;
+  const int cur0 = c->cur;
+  const long long steps0 = c->steps;
+  const bool prof0 = c->prof;
+  c->prof = false;
+  double* saved_scale = reinterpret_cast<double*>(static_cast<char*>(c->staging) + state);
+  cudaError_t e = cudaMemcpyAsync(c->staging, c->psi[cur0], state, cudaMemcpyDeviceToDevice,
+                                  c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(saved_scale, c->d_scale(), sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream);
+  auto restore = [&]() {
+    c->cur = cur0;
+    c->steps = steps0;
+    cudaError_t r = cudaMemcpyAsync(c->psi[cur0], c->staging, state, cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(c->d_scale(), saved_scale, sizeof(double), cudaMemcpyDeviceToDevice,
+                          c->stream);
+    return r;
+  };
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  int best = 0, rc = ROTGP_OK;
+  float best_ms = 0;
+  for (size_t i = 0; i < cand.size() && e == cudaSuccess && !rc; ++i) {
+    apply(cand[i]);
+    e = restore();
+    if (e != cudaSuccess) break;
+    rc = run_steps(c, 1, true);
+    if (!rc && (e = cudaEventRecord(ev[0], c->stream)) == cudaSuccess) {
+      rc = run_steps(c, steps, true);
+      if (!rc) e = cudaEventRecord(ev[1], c->stream);
+      if (!rc && e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      float ms = 0;
+      if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (!rc && e == cudaSuccess && (i == 0 || ms < best_ms)) {
+        best_ms = ms;
+        best = cand[i];
+      }
+    }
+  }
+  // then the segment count of each y/z sweep in stencil form
+  auto time_current = [&](float* ms) -> bool {
+    if ((e = restore()) != cudaSuccess) return false;
+    if ((rc = run_steps(c, 1, true))) return false;
+    if ((e = cudaEventRecord(ev[0], c->stream)) != cudaSuccess) return false;
+    if ((rc = run_steps(c, steps, true))) return false;
+    if ((e = cudaEventRecord(ev[1], c->stream)) != cudaSuccess) return false;
+    if ((e = cudaEventSynchronize(ev[1])) != cudaSuccess) return false;
+    return (e = cudaEventElapsedTime(ms, ev[0], ev[1])) == cudaSuccess;
+  };
+  apply(best);
+  for (int ax = 1; ax < dim && e == cudaSuccess && !rc; ++ax) {
+    AxisPlan& ap = c->axis[ax];
+    if (!ap.use_stencil) continue;
+    int best_s = ap.lsegs;
+    for (int sg : {1, 2, 4, 8}) {
+      if (sg == best_s || sg > ap.len / 16) continue;
+      const int keep = ap.lsegs;
+      ap.lsegs = sg;
+      float ms = 0;
+      if (!time_current(&ms)) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_s = sg;
+      }
+      ap.lsegs = keep;
+    }
+    ap.lsegs = best_s;
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  const cudaError_t er = restore();
+  c->prof = prof0;
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+  if (er != cudaSuccess) return cuda_fail(c, er, "autotune restore");
+  if (choice) *choice = best;
+  return check_flags(c);
 }
 
 int rotgp_profile_enable(rotgp_ctx* c, int on) {

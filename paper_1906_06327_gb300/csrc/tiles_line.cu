@@ -4,8 +4,10 @@
 // complex float, for lines that are strided in memory.
 //
 // A CTA of two warps owns a patch of 32 x 2 lines (32 consecutive x, 2
-// consecutive positions of the other transverse axis) and streams the whole
-// lines through an 8-slot ring of TMA boxes of 8 line positions each (4 KB):
+// consecutive positions of the other transverse axis) and one segment of
+// them (the whole lines, or a part with K-point halos read from the
+// neighbouring segments when more warps are wanted), which it streams
+// through an 8-slot ring of TMA boxes of 8 line positions each (4 KB):
 // the box of positions 8b - K .. 8b + 7 - K lands in slot b % 8 while the
 // CTA works on earlier boxes, and a slot is refilled as soon as both warps
 // are done with it, so up to seven boxes per CTA are in flight.  A warp's
@@ -36,12 +38,15 @@ __global__ void __launch_bounds__(64) k_line_pass(const __grid_constant__ CUtens
   __shared__ __align__(128) float2 ring[kSlots * kSlot];
   __shared__ __align__(8) uint64_t full[kSlots];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int px = blockIdx.x % a.tiles_x, pt = blockIdx.x / a.tiles_x;
+  const int px = blockIdx.x % a.tiles_x, pt = (blockIdx.x / a.tiles_x) % a.tiles_y;
+  const int sg = blockIdx.x / (a.tiles_x * a.tiles_y);  // segment of the lines
   const int N = AX == 2 ? a.nz : a.ny;
   const int NT = AX == 2 ? a.ny : a.nz;
   const int B = AX == 2 ? a.bz : a.by;
   const int x = 32 * px + lane, t2 = kRows * pt + w;
-  const int nb = (N + 2 * K + kBox - 1) / kBox;  // boxes over positions -K .. N-1+K
+  // outputs sb .. se-1 of this segment, from positions sb-K .. se-1+K
+  const int sb = sg * a.seg_len, se = min(N, sb + a.seg_len);
+  const int nb = (se - sb + 2 * K + kBox - 1) / kBox;
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < kSlots; ++i) mbar_init(&full[i], 1);
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(64) k_line_pass(const __grid_constant__ CUtens
   }
   __syncthreads();
   auto issue = [&](int b) {
-    const int c = kBox * b - K;
+    const int c = sb + kBox * b - K;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&full[b % kSlots], kBoxBytes);
     if (AX == 2)
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(64) k_line_pass(const __grid_constant__ CUtens
 #pragma unroll
     for (int j = 0; j < kBox; ++j)
       u[2 * K + j] = sl[(AX == 2 ? j * kRows + w : w * kBox + j) * 32 + lane];
-    const int s0 = kBox * b - 2 * K;  // output position of j = 0
+    const int s0 = sb + kBox * b - 2 * K;  // output position of j = 0
     float2 r[kBox];
     if (s0 >= B && s0 + kBox <= N - B) {
       // interior box: eight independent outputs, no branches
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(64) k_line_pass(const __grid_constant__ CUtens
 #pragma unroll
     for (int j = 0; j < kBox; ++j) {
       const int s = s0 + j;
-      if (store_ok && s >= 0 && s < N) {
+      if (store_ok && s >= sb && s < se) {
         out[(size_t)s * ostep] = r[j];
         if (REDUCE) acc.add(fmaf(r[j].x, r[j].x, r[j].y * r[j].y));
       }

@@ -37,7 +37,8 @@ ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECU
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
            "rotgp_set_omega", "rotgp_init_analytic", "rotgp_set_psi", "rotgp_get_psi",
            "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
-           "rotgp_info", "rotgp_tune", "rotgp_set_solver", "rotgp_profile_enable",
+           "rotgp_info", "rotgp_tune", "rotgp_set_solver", "rotgp_autotune",
+           "rotgp_profile_enable",
            "rotgp_profile_read",
            "rotgp_observables_noalloc")
 
@@ -119,6 +120,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_info.argtypes = [vp, ctypes.POINTER(SolverInfo)]
         lib.rotgp_tune.argtypes = [vp, ip, ip, ip, ip, ip, ip]
         lib.rotgp_set_solver.argtypes = [vp, ip, ip]
+        lib.rotgp_autotune.argtypes = [vp, ip, ctypes.POINTER(ip)]
         lib.rotgp_profile_enable.argtypes = [vp, ip]
         lib.rotgp_profile_read.argtypes = [vp, ctypes.POINTER(KStat), ip, ctypes.POINTER(ip)]
         lib.rotgp_observables_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Phys), ip,
@@ -248,6 +250,17 @@ class Solver:
              segments: int):
         self._check(self._lib.rotgp_tune(self._h, int(axis), int(lines_per_lane), int(chunk),
                                          int(ring), int(warps_per_block), int(segments)))
+
+    def autotune(self, steps: int = 5) -> dict:
+        """Time the solver forms on this context and keep the fastest (see
+        rotgp_autotune); returns the chosen form per axis."""
+        ch = ctypes.c_int(0)
+        self._check(self._lib.rotgp_autotune(self._h, int(steps), ctypes.byref(ch)))
+        m = ch.value
+        form = ["stencil" if (m >> a) & 1 else "thomas" for a in range(self.dim)]
+        if m & 8:
+            form[0] = form[1] = "fused"
+        return {"choice": m, "forms": form}
 
     def set_solver(self, axis: int, solver: str):
         """solver: "thomas", "stencil" or "fused" (see rotgp_set_solver)."""

@@ -300,6 +300,13 @@ def test_stencil_forms_match_thomas_fp32(n, h, imag):
             sep.set_solver(axis, "stencil")
         assert sep.info()["fused_xy"] == 0
         forms["stencil"] = sep
+    if len(n) == 3 or n[1] >= 48:
+        seg = Solver(n, h, precision="fp32", **phys)
+        for axis in range(1, len(n)):
+            seg.set_solver(axis, "stencil")
+            seg.tune(axis, 2, 8, 3, 1, 3)  # three segments per line (ragged)
+            assert seg.info()["segments"][axis] == 3
+        forms["stencil_segments"] = seg
     th = Solver(n, h, precision="fp32", **phys)  # the default form
     assert all(t == 0 for t in th.info()["stencil_taps"]) and th.info()["fused_xy"] == 0
     forms["thomas"] = th
@@ -342,3 +349,26 @@ def test_fused_pass_selection():
     assert d.info()["fused_xy"] == 0
     with pytest.raises(RotgpError):
         d.set_solver(0, "fused")
+
+
+@pytest.mark.parametrize("n,h", [((96, 64), (0.12, 0.15)), ((40, 36, 32), (0.3, 0.3, 0.25))])
+def test_autotune_restores_state_and_keeps_parity(n, h):
+    """The autotuner times the forms on a copy of the state: the state, the
+    step counter and the results of later steps are those of an untuned
+    context up to float rounding."""
+    phys = dict(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3)
+    R = inputs.random_phase_field(n[0], n[1], 3)
+    a = Solver(n, h, precision="fp32", **phys)
+    b = Solver(n, h, precision="fp32", **phys)
+    for s in (a, b):
+        s.init_analytic(1, R, 1.0, 1.0)
+        s.step_imag(3)
+    before = a.get_psi()
+    choice = a.autotune(steps=2)
+    assert set(choice["forms"]) <= {"thomas", "stencil", "fused"}
+    assert np.array_equal(a.get_psi(), before)
+    assert a.observables()["step"] == 3
+    for s in (a, b):
+        s.step_imag(10)
+    pa, pb = a.get_psi(), b.get_psi()
+    assert np.max(np.abs(pa - pb)) <= 5e-6 * np.max(np.abs(pb))

@@ -133,6 +133,17 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """The largest of every rank's value (the job's time is its slowest
+    rank's); value itself when dist is None."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _workload(name):
     from paper_1906_06327_gb300 import inputs
     if name not in inputs.WORKLOADS:
@@ -260,9 +271,7 @@ def run_ours(a, w):
     ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_ms = sum(ms)
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
         dist.barrier()
     updates = w.sites * a.inner * a.steps * world
     value = updates / (total_ms * 1e-3)

@@ -215,6 +215,14 @@ int rotgp_set_solver(rotgp_ctx* ctx, int axis, int solver);
  * ROTGP_EINVAL if steps < 1. */
 int rotgp_autotune(rotgp_ctx* ctx, int steps, int* choice);
 
+/* Check of the bounded device waits of the TMA tile passes: runs one CTA
+ * whose wait on a shared-memory barrier can never be satisfied (it is armed
+ * for 16 bytes that no copy delivers).  The wait must give up by itself
+ * after its bound (about 2 s of device time) and the kernel return
+ * normally.  ROTGP_OK when it did (*seconds, if not NULL, receives the
+ * device time the wait took), ROTGP_ECUDA otherwise.  Synchronises stream. */
+int rotgp_check_bounded_wait(void* stream, double* seconds);
+
 /* Per-kernel CUDA-event timing.  While enabled, every kernel launch of the
  * context is bracketed by events on its stream.  rotgp_profile_read
  * synchronises, fills up to max records (one per kernel name), sets *count

@@ -1228,6 +1228,33 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
     return (e = cudaEventElapsedTime(ms, ev[0], ev[1])) == cudaSuccess;
   };
   apply(best);
+  // segment counts of the Thomas sweeps (the number of warps decides how
+  // many waves of resident warps a launch takes)
+  for (int ax = 0; ax < dim && e == cudaSuccess && !rc; ++ax) {
+    AxisPlan& ap = c->axis[ax];
+    if (ap.use_stencil || (ax <= 1 && c->fuse_xy)) continue;
+    const AxisPlan keep = ap;
+    int best_s = ap.nseg;
+    const int nch = (ap.len + ap.sh.C - 1) / ap.sh.C;
+    for (int sg : {1, 2, 3, 4, 6, 8, 12, 16}) {
+      if (sg == keep.nseg || sg > nch) continue;
+      if (set_shape(c, ax, ap.sh.V, ap.sh.C, ap.sh.R, ap.sh.warps_per_block, sg) != ROTGP_OK)
+        continue;
+      if ((size_t)ap.sh.blocks > c->partial_doubles && ax == dim - 1) {
+        ap = keep;
+        continue;
+      }
+      float ms = 0;
+      if (!time_current(&ms)) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_s = ap.nseg;
+      }
+      ap = keep;
+    }
+    if (best_s != keep.nseg)
+      set_shape(c, ax, keep.sh.V, keep.sh.C, keep.sh.R, keep.sh.warps_per_block, best_s);
+  }
   for (int ax = 1; ax < dim && e == cudaSuccess && !rc; ++ax) {
     AxisPlan& ap = c->axis[ax];
     if (!ap.use_stencil) continue;

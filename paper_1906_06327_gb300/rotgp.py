@@ -38,6 +38,7 @@ EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys"
            "rotgp_set_omega", "rotgp_init_analytic", "rotgp_set_psi", "rotgp_get_psi",
            "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
            "rotgp_info", "rotgp_tune", "rotgp_set_solver", "rotgp_autotune",
+           "rotgp_check_bounded_wait",
            "rotgp_profile_enable",
            "rotgp_profile_read",
            "rotgp_observables_noalloc")
@@ -121,6 +122,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_tune.argtypes = [vp, ip, ip, ip, ip, ip, ip]
         lib.rotgp_set_solver.argtypes = [vp, ip, ip]
         lib.rotgp_autotune.argtypes = [vp, ip, ctypes.POINTER(ip)]
+        lib.rotgp_check_bounded_wait.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.rotgp_profile_enable.argtypes = [vp, ip]
         lib.rotgp_profile_read.argtypes = [vp, ctypes.POINTER(KStat), ip, ctypes.POINTER(ip)]
         lib.rotgp_observables_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Phys), ip,
@@ -279,6 +281,17 @@ class Solver:
         return {r.name.decode(): {"launches": r.launches, "total_ms": r.total_ms,
                                   "bytes_per_launch": r.bytes_per_launch}
                 for r in recs[:cnt.value]}
+
+
+def check_bounded_wait(stream=0) -> float:
+    """Run the bounded-wait check (rotgp_check_bounded_wait); returns the
+    device seconds the wait took before giving up."""
+    lib = load()
+    sec = ctypes.c_double(0.0)
+    rc = lib.rotgp_check_bounded_wait(ctypes.c_void_p(int(stream)), ctypes.byref(sec))
+    if rc != ROTGP_OK:
+        raise RotgpError(rc, "the bounded wait did not give up as designed")
+    return sec.value
 
 
 def observables_noalloc(n, h, psi, *, gamma=1.0, nu=1.0, lam=1.0, g=0.0, omega=0.0,

@@ -372,3 +372,17 @@ def test_autotune_restores_state_and_keeps_parity(n, h):
         s.step_imag(10)
     pa, pb = a.get_psi(), b.get_psi()
     assert np.max(np.abs(pa - pb)) <= 5e-6 * np.max(np.abs(pb))
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """A device wait that can never be satisfied gives up by itself (about
+    2 s of device time) and the kernel returns normally; the context then
+    still steps correctly."""
+    from paper_1906_06327_gb300.rotgp import check_bounded_wait
+    sec = check_bounded_wait()
+    assert 0.5 < sec < 10.0, sec
+    n, h = (40, 36), (0.3, 0.3)
+    s = Solver(n, h, precision="fp32", gamma=1.0, nu=1.0, g=20.0, omega=0.3, dt=1e-3)
+    s.init_analytic(1, inputs.random_phase_field(n[0], n[1], 0), 1.0, 1.0)
+    s.step_imag(5)
+    assert abs(s.observables()["norm"] - 1.0) < 1e-5

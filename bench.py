@@ -235,7 +235,7 @@ def run_ours(a, w):
             s.set_solver(0, "fused")
         tuned = {"choice": -1, "forms": forms}
     elif a.autotune:
-        tuned = s.autotune(steps=3)
+        tuned = s.autotune(steps=10)
     else:
         tuned = {"choice": 0, "forms": ["thomas"] * len(w.n)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")

@@ -3,6 +3,7 @@
 // into the x sweep, then the y sweep and, in 3D, the z sweep, with the norm
 // reduced in the last sweep), observables, state I/O and kernel timing.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -1200,61 +1201,69 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
   if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
   int best = 0, rc = ROTGP_OK;
   float best_ms = 0;
-  for (size_t i = 0; i < cand.size() && e == cudaSuccess && !rc; ++i) {
-    apply(cand[i]);
-    e = restore();
-    if (e != cudaSuccess) break;
-    rc = run_steps(c, 1, true);
-    if (!rc && (e = cudaEventRecord(ev[0], c->stream)) == cudaSuccess) {
-      rc = run_steps(c, steps, true);
-      if (!rc) e = cudaEventRecord(ev[1], c->stream);
-      if (!rc && e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-      float ms = 0;
-      if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      if (!rc && e == cudaSuccess && (i == 0 || ms < best_ms)) {
-        best_ms = ms;
-        best = cand[i];
-      }
-    }
-  }
-  // then the segment count of each y/z sweep in stencil form
+  // the current form and shapes: the faster of two timed repeats
   auto time_current = [&](float* ms) -> bool {
     if ((e = restore()) != cudaSuccess) return false;
     if ((rc = run_steps(c, 1, true))) return false;
-    if ((e = cudaEventRecord(ev[0], c->stream)) != cudaSuccess) return false;
-    if ((rc = run_steps(c, steps, true))) return false;
-    if ((e = cudaEventRecord(ev[1], c->stream)) != cudaSuccess) return false;
-    if ((e = cudaEventSynchronize(ev[1])) != cudaSuccess) return false;
-    return (e = cudaEventElapsedTime(ms, ev[0], ev[1])) == cudaSuccess;
+    *ms = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      float t = 0;
+      if ((e = cudaEventRecord(ev[0], c->stream)) != cudaSuccess) return false;
+      if ((rc = run_steps(c, steps, true))) return false;
+      if ((e = cudaEventRecord(ev[1], c->stream)) != cudaSuccess) return false;
+      if ((e = cudaEventSynchronize(ev[1])) != cudaSuccess) return false;
+      if ((e = cudaEventElapsedTime(&t, ev[0], ev[1])) != cudaSuccess) return false;
+      *ms = rep == 0 ? t : std::min(*ms, t);
+    }
+    return true;
   };
+  for (size_t i = 0; i < cand.size() && e == cudaSuccess && !rc; ++i) {
+    apply(cand[i]);
+    float ms = 0;
+    if (!time_current(&ms)) break;
+    if (i == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = cand[i];
+    }
+  }
   apply(best);
-  // segment counts of the Thomas sweeps (the number of warps decides how
-  // many waves of resident warps a launch takes)
+  // then the launch shapes of the Thomas sweeps (chunk, ring, segments: the
+  // number of warps decides how many waves of resident warps a launch takes)
   for (int ax = 0; ax < dim && e == cudaSuccess && !rc; ++ax) {
     AxisPlan& ap = c->axis[ax];
     if (ap.use_stencil || (ax <= 1 && c->fuse_xy)) continue;
-    const AxisPlan keep = ap;
-    int best_s = ap.nseg;
-    const int nch = (ap.len + ap.sh.C - 1) / ap.sh.C;
-    for (int sg : {1, 2, 3, 4, 6, 8, 12, 16}) {
-      if (sg == keep.nseg || sg > nch) continue;
-      if (set_shape(c, ax, ap.sh.V, ap.sh.C, ap.sh.R, ap.sh.warps_per_block, sg) != ROTGP_OK)
-        continue;
-      if ((size_t)ap.sh.blocks > c->partial_doubles && ax == dim - 1) {
+    // chunk length and ring depth first (segment count kept), then segments
+    for (int phase = 0; phase < 2 && e == cudaSuccess && !rc; ++phase) {
+      const AxisPlan keep = ap;
+      AxisPlan best_plan = keep;
+      std::vector<std::array<int, 3>> shapes;  // {C, R, segments}
+      if (phase == 0) {
+        for (int C : {8, 16, 64})
+          for (int R : {3, 4}) shapes.push_back({C, R, keep.nseg});
+      } else {
+        for (int sg : {1, 2, 3, 4, 6, 8, 12, 16}) shapes.push_back({keep.sh.C, keep.sh.R, sg});
+      }
+      for (const auto& sh : shapes) {
+        if (sh[0] == keep.sh.C && sh[1] == keep.sh.R && sh[2] == keep.nseg) continue;
+        if (!sweep_shape_built(c->fp64, keep.sh.V, sh[0])) continue;
+        if (set_shape(c, ax, keep.sh.V, sh[0], sh[1], keep.sh.warps_per_block, sh[2]) !=
+                ROTGP_OK ||
+            ap.nseg != sh[2] || ((size_t)ap.sh.blocks > c->partial_doubles && ax == dim - 1)) {
+          ap = keep;
+          continue;
+        }
+        float ms = 0;
+        if (!time_current(&ms)) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_plan = ap;
+        }
         ap = keep;
-        continue;
       }
-      float ms = 0;
-      if (!time_current(&ms)) break;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_s = ap.nseg;
-      }
-      ap = keep;
+      ap = best_plan;
     }
-    if (best_s != keep.nseg)
-      set_shape(c, ax, keep.sh.V, keep.sh.C, keep.sh.R, keep.sh.warps_per_block, best_s);
   }
+  // and the segment count of each y/z sweep in stencil form
   for (int ax = 1; ax < dim && e == cudaSuccess && !rc; ++ax) {
     AxisPlan& ap = c->axis[ax];
     if (!ap.use_stencil) continue;

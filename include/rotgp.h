@@ -255,6 +255,47 @@ int rotgp_profile_read(rotgp_ctx* ctx, rotgp_kstat* out, int max, int* count);
 int rotgp_observables_noalloc(const rotgp_grid* grid, const rotgp_phys* phys, int precision,
                               const void* psi_device, void* stream, rotgp_obs* out);
 
+/* ------------------------------------------------------------------ batch
+ * Many independent condensates (each its own grid and physics) advanced
+ * together.  The paper has no batched form; this serves workloads of many
+ * small instances (parameter sweeps).  Each instance is a context on a
+ * stream of the batch's own; a block of n steps of all active instances is
+ * captured once as a CUDA graph (fork from the batch stream into the
+ * instance streams, join back) and replayed, so that small instances run
+ * side by side and the block costs one graph launch.  All calls are ordered
+ * after earlier work on the caller's stream and before its later work.
+ * Results are those of the same steps on single contexts, bit for bit. */
+typedef struct rotgp_batch rotgp_batch;
+
+/* count instances; grids[i], phys[i] as for rotgp_create; stream = the
+ * caller's cudaStream_t.  Errors as rotgp_create (message: NULL batch). */
+int rotgp_batch_create(int count, const rotgp_grid* grids, const rotgp_phys* phys,
+                       int precision, void* stream, rotgp_batch** out);
+void rotgp_batch_destroy(rotgp_batch* batch);
+const char* rotgp_batch_last_error(const rotgp_batch* batch);
+int rotgp_batch_count(const rotgp_batch* batch);
+/* The context of instance `index` (owned by the batch; valid until
+ * rotgp_batch_destroy): initial states, I/O, solver controls. */
+int rotgp_batch_context(rotgp_batch* batch, int index, rotgp_ctx** ctx);
+/* rotgp_autotune on every instance (invalidates captured graphs). */
+int rotgp_batch_autotune(rotgp_batch* batch, int steps);
+/* n steps of every instance, imaginary (imag = 1) or real time; use_graph =
+ * 1 captures/replays a CUDA graph, 0 launches the kernels directly. */
+int rotgp_batch_step(rotgp_batch* batch, long long n, int imag, int use_graph);
+/* Synchronise; reports device-side errors of any instance. */
+int rotgp_batch_sync(rotgp_batch* batch);
+/* rotgp_observables of every instance into out[0 .. count-1]. */
+int rotgp_batch_observables(rotgp_batch* batch, rotgp_obs* out);
+/* Imaginary time until each instance converges: every check_every steps
+ * the active instances' mu is compared with the previous check; instance i
+ * is converged when |mu - mu_prev| <= rel_tol |mu| and its vortex count is
+ * unchanged, and is then left out of later steps.  Stops after max_steps.
+ * steps_out[i] = the steps instance i took; converged_out[i] (if not NULL)
+ * = 1 if it converged. */
+int rotgp_batch_converge(rotgp_batch* batch, double rel_tol, long long check_every,
+                         long long max_steps, int use_graph, long long* steps_out,
+                         int* converged_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct rotgp_ctx;
+
 namespace rotgp {
 
 template <class T>
@@ -207,5 +209,12 @@ cudaError_t launch_pack(bool fp64_store, bool fp64_src, const void* src, void* p
 cudaError_t launch_unpack(bool fp64_store, bool fp64_dst, const void* psi, void* dst, int nx,
                           int ny, int nz, int dim, const double* scale, cudaStream_t s);
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s);
+
+// Context bookkeeping for graph replay (batch.cu): which ping-pong buffer
+// holds the state, and the step counter.
+int ctx_buffer(const rotgp_ctx* c);
+void ctx_set_buffer(rotgp_ctx* c, int cur);
+long long ctx_steps(const rotgp_ctx* c);
+void ctx_add_steps(rotgp_ctx* c, long long n);
 
 }  // namespace rotgp

@@ -716,6 +716,11 @@ int encode_state_map(CUtensorMap* map, void* base, int nx, int ny, int nz, unsig
                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
+int ctx_buffer(const rotgp_ctx* c) { return c->cur; }
+void ctx_set_buffer(rotgp_ctx* c, int cur) { c->cur = cur; }
+long long ctx_steps(const rotgp_ctx* c) { return c->steps; }
+void ctx_add_steps(rotgp_ctx* c, long long n) { c->steps += n; }
+
 // Message returned by rotgp_last_error(NULL) on this thread.
 void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
 }  // namespace rotgp

@@ -97,3 +97,25 @@ WL_2D_4096_FP32 = Workload("2d-4096-fp32", (4096, 4096), (0.01, 0.01), 1.0, 1.05
 
 WORKLOADS = {w.name: w for w in (WL_2D_128_FP64, WL_2D_512_FP32, WL_3D_256_FP32,
                                  WL_2D_4096_FP32)}
+
+
+def batch_specs(count: int = 64, seed: int = 0, dt: float = 5e-4) -> list:
+    """Instances of the batched 2D workload, seeded: N drawn from
+    {128, 256, 384, 512}, Omega ~ U[0.3, 0.95], g ~ U[100, 2000],
+    nu ~ U[1.0, 1.1], gamma = 1; the domain half-width is 1.3 R_TF + 2 with
+    the Thomas-Fermi radius R_TF = (4 g / (pi (1 - Omega^2)))^(1/4), so that
+    h = 2 (1.3 R_TF + 2) / N; dt = 5e-4 for every instance.  Uniform numbers
+    come from SplitMix64(seed), five per instance."""
+    u = splitmix64(seed, 5 * count).astype(np.float64) / 2.0**64
+    out = []
+    for i in range(count):
+        r = u[5 * i:5 * i + 5]
+        n = (128, 256, 384, 512)[min(3, int(r[0] * 4))]
+        omega = 0.3 + 0.65 * r[1]
+        g = 100.0 + 1900.0 * r[2]
+        nu = 1.0 + 0.1 * r[3]
+        r_tf = (4.0 * g / (np.pi * (1.0 - omega * omega))) ** 0.25
+        h = 2.0 * (1.3 * r_tf + 2.0) / n
+        out.append(dict(n=(n, n), h=(float(h), float(h)), gamma=1.0, nu=float(nu), g=float(g),
+                        omega=float(omega), dt=dt, seed=int(r[4] * 2**31)))
+    return out

@@ -41,7 +41,11 @@ EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys"
            "rotgp_check_bounded_wait",
            "rotgp_profile_enable",
            "rotgp_profile_read",
-           "rotgp_observables_noalloc")
+           "rotgp_observables_noalloc",
+           "rotgp_batch_create", "rotgp_batch_destroy", "rotgp_batch_last_error",
+           "rotgp_batch_count", "rotgp_batch_context", "rotgp_batch_autotune",
+           "rotgp_batch_step", "rotgp_batch_sync", "rotgp_batch_observables",
+           "rotgp_batch_converge")
 
 
 class Grid(ctypes.Structure):
@@ -127,6 +131,21 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_profile_read.argtypes = [vp, ctypes.POINTER(KStat), ip, ctypes.POINTER(ip)]
         lib.rotgp_observables_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Phys), ip,
                                                   vp, vp, ctypes.POINTER(Obs)]
+        ll = ctypes.c_longlong
+        lib.rotgp_batch_create.argtypes = [ip, ctypes.POINTER(Grid), ctypes.POINTER(Phys), ip, vp,
+                                           ctypes.POINTER(vp)]
+        lib.rotgp_batch_destroy.argtypes = [vp]
+        lib.rotgp_batch_destroy.restype = None
+        lib.rotgp_batch_last_error.argtypes = [vp]
+        lib.rotgp_batch_last_error.restype = ctypes.c_char_p
+        lib.rotgp_batch_count.argtypes = [vp]
+        lib.rotgp_batch_context.argtypes = [vp, ip, ctypes.POINTER(vp)]
+        lib.rotgp_batch_autotune.argtypes = [vp, ip]
+        lib.rotgp_batch_step.argtypes = [vp, ll, ip, ip]
+        lib.rotgp_batch_sync.argtypes = [vp]
+        lib.rotgp_batch_observables.argtypes = [vp, ctypes.POINTER(Obs)]
+        lib.rotgp_batch_converge.argtypes = [vp, ctypes.c_double, ll, ll, ip,
+                                             ctypes.POINTER(ll), ctypes.POINTER(ip)]
         _lib = lib
         return lib
 
@@ -143,7 +162,7 @@ class Solver:
     """
 
     def __init__(self, n, h, *, gamma=1.0, nu=1.0, lam=1.0, g=0.0, omega=0.0, dt=1e-3,
-                 precision="fp32", stream=0):
+                 precision="fp32", stream=0, _borrowed=None):
         self._lib = load()
         self.n, self.h = tuple(int(v) for v in n), tuple(float(v) for v in h)
         self.dim = len(self.n)
@@ -151,6 +170,11 @@ class Solver:
         grid = Grid(self.dim, (ctypes.c_int * 3)(*(list(self.n) + [0] * (3 - self.dim))),
                     (ctypes.c_double * 3)(*(list(self.h) + [0.0] * (3 - self.dim))))
         self.phys = Phys(gamma, nu, lam, g, omega, dt)
+        self._owned = _borrowed is None
+        if _borrowed is not None:
+            # a context owned by a Batch
+            self._h = _borrowed
+            return
         handle = ctypes.c_void_p()
         rc = self._lib.rotgp_create(ctypes.byref(grid), ctypes.byref(self.phys),
                                     ROTGP_FP64 if self.fp64 else ROTGP_FP32,
@@ -166,7 +190,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._lib.rotgp_destroy(self._h)
+            if getattr(self, "_owned", True):
+                self._lib.rotgp_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -281,6 +306,85 @@ class Solver:
         return {r.name.decode(): {"launches": r.launches, "total_ms": r.total_ms,
                                   "bytes_per_launch": r.bytes_per_launch}
                 for r in recs[:cnt.value]}
+
+
+class Batch:
+    """Many condensates advanced together (``rotgp_batch_*``).
+
+    specs: list of dicts with keys n, h and the physics keywords of Solver;
+    precision and stream as for Solver.
+    """
+
+    def __init__(self, specs, *, precision="fp32", stream=0):
+        self._lib = load()
+        count = len(specs)
+        grids = (Grid * count)()
+        physs = (Phys * count)()
+        for i, sp in enumerate(specs):
+            n, h = list(sp["n"]), list(sp["h"])
+            dim = len(n)
+            grids[i] = Grid(dim, (ctypes.c_int * 3)(*(n + [0] * (3 - dim))),
+                            (ctypes.c_double * 3)(*(h + [0.0] * (3 - dim))))
+            physs[i] = Phys(sp.get("gamma", 1.0), sp.get("nu", 1.0), sp.get("lam", 1.0),
+                            sp.get("g", 0.0), sp.get("omega", 0.0), sp.get("dt", 1e-3))
+        handle = ctypes.c_void_p()
+        rc = self._lib.rotgp_batch_create(count, grids, physs,
+                                          ROTGP_FP64 if precision == "fp64" else ROTGP_FP32,
+                                          ctypes.c_void_p(int(stream)), ctypes.byref(handle))
+        if rc != ROTGP_OK:
+            raise RotgpError(rc, self._lib.rotgp_batch_last_error(None).decode())
+        self._h = handle
+        self.count = count
+        self.instances = []
+        for i, sp in enumerate(specs):
+            ch = ctypes.c_void_p()
+            self._check(self._lib.rotgp_batch_context(self._h, i, ctypes.byref(ch)))
+            kw = {k: sp[k] for k in ("gamma", "nu", "lam", "g", "omega", "dt") if k in sp}
+            self.instances.append(Solver(sp["n"], sp["h"], precision=precision, _borrowed=ch,
+                                         **kw))
+
+    def _check(self, rc: int):
+        if rc != ROTGP_OK:
+            raise RotgpError(rc, self._lib.rotgp_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for s in self.instances:
+                s._h = None
+            self._lib.rotgp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, steps: int = 5):
+        self._check(self._lib.rotgp_batch_autotune(self._h, int(steps)))
+
+    def step_imag(self, n: int, graph: bool = True):
+        self._check(self._lib.rotgp_batch_step(self._h, int(n), 1, int(bool(graph))))
+
+    def step_real(self, n: int, graph: bool = True):
+        self._check(self._lib.rotgp_batch_step(self._h, int(n), 0, int(bool(graph))))
+
+    def sync(self):
+        self._check(self._lib.rotgp_batch_sync(self._h))
+
+    def observables(self) -> list:
+        out = (Obs * self.count)()
+        self._check(self._lib.rotgp_batch_observables(self._h, out))
+        return [o.as_dict() for o in out]
+
+    def converge(self, rel_tol: float, check_every: int, max_steps: int, graph: bool = True):
+        """Returns (steps per instance, converged flags)."""
+        steps = (ctypes.c_longlong * self.count)()
+        conv = (ctypes.c_int * self.count)()
+        self._check(self._lib.rotgp_batch_converge(self._h, float(rel_tol), int(check_every),
+                                                   int(max_steps), int(bool(graph)), steps,
+                                                   conv))
+        return list(steps), [bool(c) for c in conv]
 
 
 def check_bounded_wait(stream=0) -> float:

@@ -164,7 +164,7 @@ struct sweep_shape {
 cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis_coef& co,
                           cudaStream_t s);
 cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,
-                           cudaStream_t s);
+                           const void* map, cudaStream_t s);  // map: rows TMA map or null
 cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
                                  const sweep_shape& sh, cudaStream_t s);
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);

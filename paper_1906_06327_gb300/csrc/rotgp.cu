@@ -85,7 +85,11 @@ struct rotgp_ctx {
   // (fuse_xy), and the y/z stencil sweeps; TMA maps per state buffer
   bool maps_ok = false;
   bool fuse_ok = false, fuse_xy = false;
+  bool x_tma = true;  // Thomas x sweep loads its chunks with TMA (when the maps exist)
   CUtensorMap map_xy[2], map_y[2], map_z[2];
+  // rows maps of the Thomas x sweep's TMA chunk loads: [buffer][C = 8, 16]
+  bool xmaps_ok = false;
+  CUtensorMap map_x[2][2];
   double* partials = nullptr;
   size_t partial_doubles = 0;
   unsigned* counter = nullptr;
@@ -446,6 +450,14 @@ void build_maps(rotgp_ctx* c) {
     ok = ok && encode_state_map(&c->map_y[b], c->psi[b], c->nx, c->ny, c->nz, 64, 8, rows) == 0;
     ok = ok && encode_state_map(&c->map_z[b], c->psi[b], c->nx, c->ny, c->nz, 64, rows, 8) == 0;
   }
+  // the Thomas x sweep: boxes of 64 rows x (C + 2) points
+  c->xmaps_ok = !c->fp64 && c->nx % 2 == 0;
+  for (int b = 0; b < 2 && c->xmaps_ok; ++b)
+    for (int ci = 0; ci < 2 && c->xmaps_ok; ++ci) {
+      const int C = ci == 0 ? 8 : 16;
+      c->xmaps_ok = encode_rows_map(&c->map_x[b][ci], c->psi[b], c->nx,
+                                    (long long)c->ny * c->nz, 2 * (C + 2), 64) == 0;
+    }
   c->maps_ok = ok;
   if (!ok) {
     c->fuse_ok = c->fuse_xy = false;
@@ -609,7 +621,10 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
       const long long warps = ((ap.lines + 1) / 2) * ((ap.len + 127) / 128);
       e = launch_stencil_x(imag, a, warps, c->stream);
     } else {
-      e = launch_sweep_x(c->fp64, imag, a, ap.sh, c->stream);
+      const void* xm = nullptr;
+      if (c->xmaps_ok && c->x_tma && ap.sh.V == 2 && ap.sh.vec16 && (ap.sh.C == 8 || ap.sh.C == 16))
+        xm = &c->map_x[c->cur][ap.sh.C == 8 ? 0 : 1];
+      e = launch_sweep_x(c->fp64, imag, a, ap.sh, xm, c->stream);
     }
   } else {
     a.stride = axis == 1 ? (long long)c->nx : (long long)c->nx * c->ny;
@@ -703,6 +718,19 @@ int dev_alloc(rotgp_ctx* c, void** p, size_t bytes) {
 }  // namespace
 
 namespace rotgp {
+int encode_rows_map(CUtensorMap* map, void* base, int nx, long long nrows, unsigned box0,
+                    unsigned box1) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn) return -1;
+  const cuuint64_t dims[2] = {2ull * (cuuint64_t)nx, (cuuint64_t)nrows};
+  const cuuint64_t strides[1] = {8ull * (cuuint64_t)nx};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t estr[2] = {1, 1};
+  return (int)fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 int encode_state_map(CUtensorMap* map, void* base, int nx, int ny, int nz, unsigned box0,
                      unsigned box1, unsigned box2) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();

@@ -11,6 +11,7 @@
 // same slot for coalesced stores.  The solver and the ring are described in
 // sweep_common.cuh.
 #include "sweep_common.cuh"
+#include "tma.cuh"
 
 namespace rotgp {
 
@@ -230,8 +231,13 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
 // run as packed FP32x2 arithmetic (sweep_common.cuh).  The ring keeps each
 // row interleaved (the cooperative copies and stores need that); rows are
 // split on the 16-byte shared loads and joined on the stores.
-template <int C, bool IMAG, bool VEC16>
-__global__ void __launch_bounds__(128) k_sweep_x2(const stream_args a) {
+//
+// TMA = true: each chunk (64 rows x C + 2 points, exactly a ring slot) is
+// one 2-D TMA box issued by lane 0 on a per-slot barrier, instead of the
+// lanes' cooperative copies (needs 16-byte rows, VEC16).
+template <int C, bool IMAG, bool VEC16, bool TMA>
+__global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtensorMap map,
+                                                  const stream_args a) {
   using E = cpx<float>;
   constexpr int EP = VEC16 ? 2 : 1;
   constexpr int PITCH = C + 2;                 // odd number of 16-byte units
@@ -240,15 +246,22 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const stream_args a) {
   constexpr int LPR = (C + 1 + EP - 1) / EP;
   constexpr int SPR = C / EP;
   static_assert(LPR * EP <= PITCH, "row pitch too small");
+  static_assert(!TMA || (VEC16 && (SLOT * 8) % 128 == 0), "TMA slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[TMA ? 4 * 4 : 1];  // [warp][slot]
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int R = a.ring;
-  if (R < 3 || R > 4 ||
-      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT) * (unsigned)sizeof(E)) {
+  const unsigned pad = TMA ? 128 : 0;  // TMA destinations start on 128 bytes
+  if (R < 3 || R > 4 || (TMA && blockDim.x > 128) ||
+      dynamic_smem_bytes() <
+          (blockDim.x >> 5) * (unsigned)(R * SLOT) * (unsigned)sizeof(E) + pad) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
   }
-  E* ring = reinterpret_cast<E*>(smem_raw) + (size_t)wib * R * SLOT;
+  unsigned char* sbase =
+      TMA ? smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127) : smem_raw;
+  E* ring = reinterpret_cast<E*>(sbase) + (size_t)wib * R * SLOT;
+  uint64_t* bar = bars + (TMA ? wib * 4 : 0);
   const long long nrows = a.nlines;
   const long long ngroups = (nrows + ROWS - 1) / ROWS;
   const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
@@ -301,8 +314,17 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const stream_args a) {
     }
     return v;
   };
-  auto slot = [&](int q) { return ring + (size_t)(q % R) * SLOT; };
+  auto slot = [&](int q) { return ring + (size_t)((q - qa) % R) * SLOT; };
   auto issue = [&](int q) {
+    if (TMA) {
+      if (q < qb && lane == 0) {
+        const int sl = (q - qa) % R;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[sl], (unsigned)(SLOT * sizeof(E)));
+        tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
+      }
+      return;
+    }
     if (q < qb) {
       E* sl = slot(q);
       for (int t = lane; t < ROWS * LPR; t += 32) {
@@ -374,11 +396,29 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const stream_args a) {
     for (int k = 0; k < C / 2; ++k) store_pair(sp, k, w[2 * k], w[2 * k + 1]);
   };
 
+  if (TMA) {
+    if (lane == 0) {
+      for (int i = 0; i < R; ++i) mbar_init(&bar[i], 1);
+      mbar_fence_init();
+    }
+    __syncwarp();
+  }
   for (int i = 0; i < R - 1; ++i) issue(qa + i);
   c2 pm = zero2(), d = zero2();
   for (int q = qa; q <= qb; ++q) {
     if (q < qb) {
-      ring_wait(R);
+      if (TMA) {
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait(&bar[(q - qa) % R], (unsigned)(((q - qa) / R) & 1)))) {
+          // a TMA load never landed: let the other loads in flight land, report, stop
+          for (int r = q + 1; r < min(q + R - 1, qb); ++r)
+            mbar_wait(&bar[(r - qa) % R], (unsigned)(((r - qa) / R) & 1));
+          if (lane == 0) atomicOr(a.flags, 4);
+          return;
+        }
+      } else {
+        ring_wait(R);
+      }
       __syncwarp();
       if (q * C >= lt && (q + 1) * C <= N)
         forward(bool_tag<true>{}, slot(q), q * C, pm, d);
@@ -426,18 +466,23 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const stream_args a) {
     __syncwarp();
     issue(q + R - 1);
   }
-  cp_async_wait<0>();
+  if (!TMA) cp_async_wait<0>();
 }
 
 template <int C>
 static cudaError_t dispatch_x2(bool imag, bool vec16, const stream_args& a, const sweep_shape& sh,
-                               cudaStream_t s) {
-  static bool done[4] = {false, false, false, false};
-  auto fn = vec16 ? (imag ? k_sweep_x2<C, true, true> : k_sweep_x2<C, false, true>)
-                  : (imag ? k_sweep_x2<C, true, false> : k_sweep_x2<C, false, false>);
-  cudaError_t e = allow_smem((const void*)fn, &done[(vec16 ? 2 : 0) + (imag ? 1 : 0)]);
+                               const void* map, cudaStream_t s) {
+  static bool done[6] = {false, false, false, false, false, false};
+  const bool tma = map != nullptr && vec16 && sh.warps_per_block <= 4;
+  static const CUtensorMap none{};
+  const CUtensorMap& m = tma ? *static_cast<const CUtensorMap*>(map) : none;
+  auto fn = tma ? (imag ? k_sweep_x2<C, true, true, true> : k_sweep_x2<C, false, true, true>)
+          : vec16 ? (imag ? k_sweep_x2<C, true, true, false> : k_sweep_x2<C, false, true, false>)
+                  : (imag ? k_sweep_x2<C, true, false, false> : k_sweep_x2<C, false, false, false>);
+  const int k = (tma ? 4 : vec16 ? 2 : 0) + (imag ? 1 : 0);
+  cudaError_t e = allow_smem((const void*)fn, &done[k]);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
+  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem + (tma ? 128 : 0), s>>>(m, a);
   return cudaGetLastError();
 }
 
@@ -456,14 +501,14 @@ static cudaError_t dispatch_x(bool imag, bool vec16, const stream_args& a, const
 // Every (precision, V, C) combination the host can choose is instantiated
 // here; anything else is rejected before a launch.
 cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,
-                           cudaStream_t s) {
+                           const void* map, cudaStream_t s) {
   if (fp64) {
     if (sh.V == 1 && sh.C == 16) return dispatch_x<double, 1, 16>(imag, true, a, sh, s);
     if (sh.V == 1 && sh.C == 64) return dispatch_x<double, 1, 64>(imag, true, a, sh, s);
     return cudaErrorInvalidValue;
   }
-  if (sh.V == 2 && sh.C == 8) return dispatch_x2<8>(imag, sh.vec16, a, sh, s);
-  if (sh.V == 2 && sh.C == 16) return dispatch_x2<16>(imag, sh.vec16, a, sh, s);
+  if (sh.V == 2 && sh.C == 8) return dispatch_x2<8>(imag, sh.vec16, a, sh, map, s);
+  if (sh.V == 2 && sh.C == 16) return dispatch_x2<16>(imag, sh.vec16, a, sh, map, s);
   if (sh.V == 1 && sh.C == 16) return dispatch_x<float, 1, 16>(imag, sh.vec16, a, sh, s);
   if (sh.V == 1 && sh.C == 64) return dispatch_x<float, 1, 64>(imag, sh.vec16, a, sh, s);
   return cudaErrorInvalidValue;

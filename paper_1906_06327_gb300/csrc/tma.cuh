@@ -73,6 +73,22 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 2-D tiled TMA load of the box at element coordinates (c0, c1).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Host: encode a 2-D float32 tensor map over the rows of a complex-float
+// state (nrows rows of nx points; dimension 0 counts floats) with the box
+// (floats, rows).  Same return convention as encode_state_map.
+int encode_rows_map(CUtensorMap* map, void* base, int nx, long long nrows, unsigned box0,
+                    unsigned box1);
+
 // Host: encode a 3-D float32 tensor map over a complex-float state of
 // nx x ny x nz points (x fastest; dimension 0 counts floats, 2 per point)
 // with the given box (floats, rows, planes).  Returns a CUDA driver status

@@ -76,6 +76,11 @@ typedef struct {
  *  mu_c, energy_c  complex forms (Eqs. e2d/e3d)
  *  rms_*     sqrt(<x^2>), sqrt(<y^2>), sqrt(<z^2>) (0 in 2D), sqrt(<r^2>)
  *  max_density     max |psi|^2
+ *  mu4, energy4    the complex forms with fourth-order central differences
+ *                  for the derivatives (points beyond the grid read as
+ *                  zero), the accuracy of the energies printed in the
+ *                  paper's Table 1; mu_c and energy_c use the three-point
+ *                  differences of the CN sweeps themselves
  *  step      number of steps taken by this context
  *  vortices  sum of |winding| over plaquettes of the z = 0 plane inside 0.9
  *            of the ellipse R^2 = 6<x^2>, 6<y^2> of that plane (not in the
@@ -85,6 +90,7 @@ typedef struct {
 typedef struct {
   double norm, mu, energy, mu_c, energy_c;
   double rms_x, rms_y, rms_z, rms_r, max_density;
+  double mu4, energy4;
   long long step;
   int vortices;
   int flags;
@@ -194,6 +200,10 @@ int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring
  *   halos (the result equals the separate stencil sweeps up to float
  *   rounding).  In 2D it is the whole step.  Selecting THOMAS or STENCIL
  *   on axis 0 or 1 turns it off.
+ * The stencil and fused forms apply to imaginary-time steps only: real-time
+ * steps always use the Thomas form, whose Crank-Nicolson map stays unitary
+ * with rounded coefficients (independently rounded stencil weights would
+ * let the norm drift by ~1e-7 per step in float).
  * A new context uses ROTGP_SOLVER_THOMAS on every axis. 
  * The y and z sweeps in stencil form, and the fused pass, stage their
  * tiles with TMA loads whose waits are bounded: a wait that runs out
@@ -245,7 +255,7 @@ int rotgp_profile_read(rotgp_ctx* ctx, rotgp_kstat* out, int max, int* count);
  *  stream      cudaStream_t to run on; the call synchronises it
  *  out         host struct filled like rotgp_observables, except that step
  *              is 0 and vortices is -1 (not evaluated)
- * Scratch: a file-scope device array of 416 KiB inside the library, which
+ * Scratch: a file-scope device array of about 448 KiB inside the library, which
  * every GPU that loads the library holds until exit.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with
  * the device current; make that first call before any stream capture.  All

@@ -114,7 +114,7 @@ class Phys:
 
 
 OBS_KEYS = ("norm", "mu", "energy", "mu_c", "energy_c", "rms_x", "rms_y",
-            "rms_z", "rms_r", "max_density")
+            "rms_z", "rms_r", "max_density", "mu4", "energy4")
 
 
 def _check(rc: int, what: str):

@@ -359,6 +359,20 @@ int orc_init_analytic(int dim, const int* n, const double* h, int function,
  *   E_c  = Re sum psi^* (H_lin + g|psi|^2/2) psi / sum|psi|^2.
  * rms_a = sqrt(sum a^2 |psi|^2 / sum |psi|^2), rms_r = sqrt(<x^2>+<y^2>[+<z^2>]).
  * out[] = {norm, mu, E, mu_c, E_c, rms_x, rms_y, rms_z, rms_r, max |psi|^2}. */
+/* psi at (i, j, k), zero outside the stored grid (the Dirichlet edges
+ * extended by zero), for the five-point stencils below. */
+static cplx at_or_zero(const orc_grid* G, const cplx* psi, long long i, long long j,
+                       long long k) {
+  if (i < 0 || i >= npts(G, 0) || j < 0 || j >= npts(G, 1) || k < 0 || k >= npts(G, 2))
+    return 0.0;
+  return psi[idx3(G, i, j, k)];
+}
+
+/* Observables.  out[0..9] as listed in rotgp_obs; out[10], out[11]: mu and
+ * E in the complex form with fourth-order central differences for the
+ * derivatives (Laplacian (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2)/(12 h^2),
+ * first derivative (-f2 + 8 f1 - 8 f-1 + f-2)/(12 h)) -- the accuracy at
+ * which the paper's Table 1 energies are evaluated. */
 int orc_observables(int dim, const int* n, const double* h, const double* phys,
                     const double* psi_d, double* out) {
   orc_grid G;
@@ -370,6 +384,7 @@ int orc_observables(int dim, const int* n, const double* h, const double* phys,
   double lin_i = 0, nl_i = 0;   /* same for the phase-rotated state        */
   double lin_c = 0, nl_c = 0;   /* complex-form sums                       */
   double sx2 = 0, sy2 = 0, sz2 = 0, dmax = 0;
+  double lin_4 = 0;             /* complex form, fourth-order differences  */
   const long long sx = 1, sy = npts(&G, 0), sz = npts(&G, 0) * npts(&G, 1);
   for (long long k = 0; k < npts(&G, 2); ++k)
     for (long long j = 0; j < npts(&G, 1); ++j)
@@ -401,6 +416,19 @@ int orc_observables(int dim, const int* n, const double* h, const double* phys,
         cplx Lz = I * (y * dx - x * dy);
         cplx Hlin = -0.5 * lap + V * c - P.omega * Lz;
         lin_c += creal(conj(c) * Hlin);
+        /* fourth order: f(+-1), f(+-2) along each axis */
+        cplx lap4 = 0.0, d4[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < G.dim; ++a) {
+          const long long di = a == 0, dj = a == 1, dk = a == 2;
+          cplx p1 = at_or_zero(&G, psi, i + di, j + dj, k + dk);
+          cplx m1 = at_or_zero(&G, psi, i - di, j - dj, k - dk);
+          cplx p2 = at_or_zero(&G, psi, i + 2 * di, j + 2 * dj, k + 2 * dk);
+          cplx m2 = at_or_zero(&G, psi, i - 2 * di, j - 2 * dj, k - 2 * dk);
+          lap4 += (-p2 + 16.0 * p1 - 30.0 * c + 16.0 * m1 - m2) / (12.0 * G.h[a] * G.h[a]);
+          d4[a] = (-p2 + 8.0 * p1 - 8.0 * m1 + m2) / (12.0 * G.h[a]);
+        }
+        cplx Lz4 = I * (y * d4[0] - x * d4[1]);
+        lin_4 += creal(conj(c) * (-0.5 * lap4 + V * c - P.omega * Lz4));
         nl_c += P.g * dens * dens;
         s_abs2 += dens;
         s_r2 += re * re;
@@ -425,6 +453,8 @@ int orc_observables(int dim, const int* n, const double* h, const double* phys,
   out[7] = G.dim == 3 ? sqrt(sz2 / s_abs2) : 0.0;
   out[8] = sqrt((sx2 + sy2 + sz2) / s_abs2);
   out[9] = dmax;
+  out[10] = (lin_4 + nl_c) / s_abs2;
+  out[11] = (lin_4 + 0.5 * nl_c) / s_abs2;
   return ORC_OK;
 }
 

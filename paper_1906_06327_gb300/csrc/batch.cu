@@ -27,6 +27,7 @@ struct BatchGraph {
   long long steps = 0;
   bool imag = true;
   std::vector<int> cur0, cur1;  // state buffer of each instance before / after
+  std::vector<long long> plan;  // each instance's plan version at capture
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -88,6 +89,13 @@ int run_set(rotgp_batch* b, const std::vector<int>& set, long long n, bool imag,
 int run_set_inner(rotgp_batch* b, const std::vector<int>& set, long long n, bool imag,
                   bool use_graph) {
   cudaError_t e;
+  // work already queued on the instance streams (table rebuilds of
+  // rotgp_set_phys, state I/O) comes first
+  for (int i : set) {
+    if ((e = cudaEventRecord(b->done[i], b->streams[i])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->stream, b->done[i], 0)) != cudaSuccess)
+      return bfail(b, ROTGP_ECUDA, "order: %s", cudaGetErrorString(e));
+  }
   if (!use_graph) {
     if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess)
       return bfail(b, ROTGP_ECUDA, "fork: %s", cudaGetErrorString(e));
@@ -103,10 +111,14 @@ int run_set_inner(rotgp_batch* b, const std::vector<int>& set, long long n, bool
     return ROTGP_OK;
   }
   std::vector<int> cur(set.size());
-  for (size_t k = 0; k < set.size(); ++k) cur[k] = rotgp::ctx_buffer(b->ctx[set[k]]);
+  std::vector<long long> plan(set.size());
+  for (size_t k = 0; k < set.size(); ++k) {
+    cur[k] = rotgp::ctx_buffer(b->ctx[set[k]]);
+    plan[k] = rotgp::ctx_plan_version(b->ctx[set[k]]);
+  }
   BatchGraph* g = nullptr;
   for (auto& x : b->graphs)
-    if (x.set == set && x.steps == n && x.imag == imag && x.cur0 == cur) g = &x;
+    if (x.set == set && x.steps == n && x.imag == imag && x.cur0 == cur && x.plan == plan) g = &x;
   if (g) {
     // replay: the graph advances the states as captured
     for (size_t k = 0; k < set.size(); ++k) {
@@ -126,6 +138,7 @@ int run_set_inner(rotgp_batch* b, const std::vector<int>& set, long long n, bool
     ng.steps = n;
     ng.imag = imag;
     ng.cur0 = cur;
+    ng.plan = plan;
     if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
       return bfail(b, ROTGP_ECUDA, "begin capture: %s", cudaGetErrorString(e));
     int rc = ROTGP_OK;

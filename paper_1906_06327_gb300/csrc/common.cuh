@@ -136,8 +136,8 @@ struct obs_args {
   double* result;  // NOBS doubles
 };
 
-enum { NQ = 13 };   // partial sums per block in the observables reduction
-enum { NOBS = 10 }; // norm, mu, E, mu_c, E_c, rms_x, rms_y, rms_z, rms_r, max
+enum { NQ = 14 };   // partial sums per block in the observables reduction (last: a max)
+enum { NOBS = 12 }; // norm, mu, E, mu_c, E_c, rms_x, rms_y, rms_z, rms_r, max, mu4, E4
 
 struct vort_args {
   const void* psi;
@@ -215,6 +215,7 @@ cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s);
 int ctx_buffer(const rotgp_ctx* c);
 void ctx_set_buffer(rotgp_ctx* c, int cur);
 long long ctx_steps(const rotgp_ctx* c);
+long long ctx_plan_version(const rotgp_ctx* c);
 void ctx_add_steps(rotgp_ctx* c, long long n);
 
 }  // namespace rotgp

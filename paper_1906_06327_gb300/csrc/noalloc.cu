@@ -12,7 +12,7 @@
 // result slots and the last-block ticket) in one file-scope device array.
 //
 // That array is part of the library image: every GPU that loads the library
-// holds it (416 KiB) until the process exits.  All calls share it and it
+// holds it (about 448 KiB) until the process exits.  All calls share it and it
 // keeps the last call's contents; the ticket counter is cleared by every
 // call before its kernel runs.  Calls whose work overlaps on the GPU (for
 // example on two streams at once) race on the array and must be ordered by
@@ -38,7 +38,7 @@ constexpr long long kPointsPerBlock = 8192;    // grid points one block reduces
 constexpr long long kMaxPoints = kMaxBlocks * kPointsPerBlock;  // 33,554,432
 constexpr int kResult = kMaxBlocks * NQ;       // offset of the NOBS results
 constexpr int kTicket = kResult + NOBS;        // offset of the ticket counter
-constexpr int kScratchDoubles = kTicket + 2;   // 53,260 doubles = 416 KiB
+constexpr int kScratchDoubles = kTicket + 2;   // 57,358 doubles, about 448 KiB
 
 }  // namespace
 
@@ -119,7 +119,22 @@ __global__ void __launch_bounds__(kThreads) k_observables_noalloc(
     q[9] += (double)(x * x * dens);
     q[10] += (double)(y * y * dens);
     q[11] += (double)(z * z * dens);
-    q[12] = fmax(q[12], (double)dens);
+    {
+      // fourth-order central differences (points beyond the grid are zero)
+      const C xp2 = at(i + 2, j, k), xm2 = at(i - 2, j, k);
+      const C yp2 = at(i, j + 2, k), ym2 = at(i, j - 2, k);
+      C lap4 = (ihx2 / (T)12) * ((T)16 * (xp + xm) - xp2 - xm2 - (T)30 * c) +
+               (ihy2 / (T)12) * ((T)16 * (yp + ym) - yp2 - ym2 - (T)30 * c);
+      if (dim == 3)
+        lap4 = lap4 + (ihz2 / (T)12) * ((T)16 * (at(i, j, k + 1) + at(i, j, k - 1)) -
+                                        at(i, j, k + 2) - at(i, j, k - 2) - (T)30 * c);
+      const C dx4 = (i2hx / (T)6) * ((T)8 * (xp - xm) - xp2 + xm2);
+      const C dy4 = (i2hy / (T)6) * ((T)8 * (yp - ym) - yp2 + ym2);
+      const C lz4 = y * dx4 - x * dy4;
+      q[12] += (double)(re * ((T)-0.5 * lap4.x + V * c.x + om * lz4.y) +
+                        im * ((T)-0.5 * lap4.y + V * c.y - om * lz4.x));
+    }
+    q[13] = fmax(q[13], (double)dens);
   }
   __shared__ double ws[kThreads / 32][NQ];
   __shared__ bool last;
@@ -169,7 +184,9 @@ __global__ void __launch_bounds__(kThreads) k_observables_noalloc(
     result[6] = sqrt(fin[10] / fin[0]);
     result[7] = dim == 3 ? sqrt(fin[11] / fin[0]) : 0.0;
     result[8] = sqrt((fin[9] + fin[10] + fin[11]) / fin[0]);
-    result[9] = fin[12];
+    result[9] = fin[13];
+    result[10] = (fin[12] + fin[8]) / fin[0];
+    result[11] = (fin[12] + 0.5 * fin[8]) / fin[0];
     *ticket = 0u;
   }
 }
@@ -267,6 +284,8 @@ extern "C" int rotgp_observables_noalloc(const rotgp_grid* grid, const rotgp_phy
   out->rms_z = res[7];
   out->rms_r = res[8];
   out->max_density = res[9];
+  out->mu4 = res[10];
+  out->energy4 = res[11];
   out->step = 0;
   out->vortices = -1;
   out->flags = phys->omega >= (phys->gamma < phys->nu ? phys->gamma : phys->nu) ? 1 : 0;

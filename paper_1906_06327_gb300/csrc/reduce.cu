@@ -72,7 +72,11 @@ __device__ double combine(const double* partials, int v) {
 //   q4 g |psi|^2 psi_R^2
 //   q5, q6  the same two for the state rotated by -i (R <- I, I <- -R)
 //   q7 Re psi^* (-lap/2 + V - Omega L_z) psi, L_z = i (y D_x - x D_y)
-//   q8 g |psi|^4   q9..q11  x^2, y^2, z^2 times |psi|^2   q12 max |psi|^2
+//   q8 g |psi|^4   q9..q11  x^2, y^2, z^2 times |psi|^2
+//   q12 as q7 with fourth-order central differences (Laplacian
+//       (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2)/(12 h^2), first derivative
+//       (-f2 + 8 f1 - 8 f-1 + f-2)/(12 h); points beyond the grid are zero)
+//   q13 max |psi|^2
 template <class T>
 __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
   using C = cpx<T>;
@@ -99,6 +103,8 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
     const T vyz = (T)a.hnu2 * y * y + (T)a.hlam2 * z * z;
     const C* rp = psi + (long long)row * nx;
     const bool has_yp = j + 1 < ny, has_zp = a.dim == 3 && k + 1 < nz;
+    const bool has_yp2 = j + 2 < ny, has_ym2 = j >= 2;
+    const bool has_zp2 = a.dim == 3 && k + 2 < nz, has_zm2 = a.dim == 3 && k >= 2;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       if (i == 0) continue;
       const T x = (T)(a.x0 + (double)i * a.hx);
@@ -134,7 +140,26 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
       t[9] += x * x * dens;
       t[10] += y * y * dens;
       t[11] += z * z * dens;
-      t[12] = t[12] > dens ? t[12] : dens;
+      {
+        const C z0 = mk<T>(0, 0);
+        const C xp2 = i + 2 < nx ? s * rp[i + 2] : z0, xm2 = i >= 2 ? s * rp[i - 2] : z0;
+        const C yp2 = has_yp2 ? s * rp[i + 2 * nx] : z0, ym2 = has_ym2 ? s * rp[i - 2 * nx] : z0;
+        const T c12x = ihx2 / (T)12, c12y = ihy2 / (T)12;
+        C lap4 = c12x * ((T)16 * (xp + xm) - xp2 - xm2 - (T)30 * c) +
+                 c12y * ((T)16 * (yp + ym) - yp2 - ym2 - (T)30 * c);
+        if (a.dim == 3) {
+          const C zp = has_zp ? s * rp[i + plane] : z0, zm = s * rp[i - plane];
+          const C zp2 = has_zp2 ? s * rp[i + 2 * plane] : z0;
+          const C zm2 = has_zm2 ? s * rp[i - 2 * plane] : z0;
+          lap4 = lap4 + (ihz2 / (T)12) * ((T)16 * (zp + zm) - zp2 - zm2 - (T)30 * c);
+        }
+        const C dx4 = (i2hx / (T)6) * ((T)8 * (xp - xm) - xp2 + xm2);
+        const C dy4 = (i2hy / (T)6) * ((T)8 * (yp - ym) - yp2 + ym2);
+        const C lz4 = y * dx4 - x * dy4;
+        t[12] += re * ((T)-0.5 * lap4.x + V * c.x + om * lz4.y) +
+                 im * ((T)-0.5 * lap4.y + V * c.y - om * lz4.x);
+      }
+      t[13] = t[13] > dens ? t[13] : dens;
     }
   }
   double q[NQ];
@@ -160,7 +185,9 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
     r[6] = sqrt(fin[10] / fin[0]);
     r[7] = a.dim == 3 ? sqrt(fin[11] / fin[0]) : 0.0;
     r[8] = sqrt((fin[9] + fin[10] + fin[11]) / fin[0]);
-    r[9] = fin[12];
+    r[9] = fin[13];
+    r[10] = (fin[12] + fin[8]) / fin[0];
+    r[11] = (fin[12] + 0.5 * fin[8]) / fin[0];
     *a.counter = 0u;
   }
 }

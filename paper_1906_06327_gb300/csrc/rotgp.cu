@@ -86,6 +86,7 @@ struct rotgp_ctx {
   bool maps_ok = false;
   bool fuse_ok = false, fuse_xy = false;
   bool x_tma = true;  // Thomas x sweep loads its chunks with TMA (when the maps exist)
+  long long plan_version = 0;  // bumped whenever launches or tables change
   CUtensorMap map_xy[2], map_y[2], map_z[2];
   // rows maps of the Thomas x sweep's TMA chunk loads: [buffer][C = 8, 16]
   bool xmaps_ok = false;
@@ -617,7 +618,7 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
     a.scale = c->d_scale();
     Timed t(c, K_SWEEP_X);
-    if (ap.use_stencil && c->nx % 4 == 0) {
+    if (ap.use_stencil && imag && c->nx % 4 == 0) {
       const long long warps = ((ap.lines + 1) / 2) * ((ap.len + 127) / 128);
       e = launch_stencil_x(imag, a, warps, c->stream);
     } else {
@@ -631,7 +632,7 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.outer = axis == 1 ? (long long)c->nx * c->ny : (long long)c->nx;
     a.coef_mode = axis == 1 ? 1 : 0;
     Timed t(c, axis == 1 ? K_SWEEP_Y : K_SWEEP_Z);
-    if (ap.use_stencil) {
+    if (ap.use_stencil && imag) {
       tile_args ta = make_tile_args(c, imag);
       ta.tiles_x = (c->nx + 31) / 32;
       ta.tiles_y = ((axis == 1 ? c->nz : c->ny) + line_rows() - 1) / line_rows();
@@ -653,7 +654,10 @@ int run_steps(rotgp_ctx* c, long long n, bool imag) {
   for (long long s = 0; s < n; ++s) {
     for (int a = 0; a < c->grid.dim; ++a) {
       int rc;
-      if (a == 0 && c->fuse_xy) {
+      // the stencil and fused forms serve imaginary time; real-time steps
+      // keep the Thomas form, whose CN map stays unitary with rounded
+      // coefficients (the stencil's independently rounded weights do not)
+      if (a == 0 && c->fuse_xy && imag) {
         rc = xy_pass(c, imag);
         ++a;  // the y sweep is part of the pass
       } else {
@@ -747,6 +751,7 @@ int encode_state_map(CUtensorMap* map, void* base, int nx, int ny, int nz, unsig
 int ctx_buffer(const rotgp_ctx* c) { return c->cur; }
 void ctx_set_buffer(rotgp_ctx* c, int cur) { c->cur = cur; }
 long long ctx_steps(const rotgp_ctx* c) { return c->steps; }
+long long ctx_plan_version(const rotgp_ctx* c) { return c->plan_version; }
 void ctx_add_steps(rotgp_ctx* c, long long n) { c->steps += n; }
 
 // Message returned by rotgp_last_error(NULL) on this thread.
@@ -900,6 +905,7 @@ void rotgp_destroy(rotgp_ctx* ctx) {
 
 int rotgp_set_phys(rotgp_ctx* c, const rotgp_phys* phys) {
   if (!c || !phys) return ROTGP_EINVAL;
+  ++c->plan_version;
   if (!finite_phys(phys)) return fail(c, ROTGP_EINVAL, "physics must be finite, dt > 0");
   const rotgp_phys old = c->phys;
   c->phys = *phys;
@@ -1107,6 +1113,8 @@ int rotgp_observables(rotgp_ctx* c, rotgp_obs* out) {
   out->rms_z = r[7];
   out->rms_r = r[8];
   out->max_density = r[9];
+  out->mu4 = r[10];
+  out->energy4 = r[11];
   int cnt = 0;
   std::memcpy(&cnt, c->h_obs + NOBS, sizeof(int));
   out->vortices = cnt;
@@ -1144,6 +1152,7 @@ int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
 int rotgp_tune(rotgp_ctx* c, int axis, int lines_per_lane, int chunk, int ring,
                int warps_per_block, int segments) {
   if (!c) return ROTGP_EINVAL;
+  ++c->plan_version;
   if (axis >= 1 && axis < c->grid.dim && c->axis[axis].use_stencil) {
     // stencil form of a y or z sweep: only the segment count applies
     if (segments < 1 || segments > kMaxLineSegs || segments > c->axis[axis].len / 8)
@@ -1167,6 +1176,7 @@ int rotgp_tune(rotgp_ctx* c, int axis, int lines_per_lane, int chunk, int ring,
 
 int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
   if (!c) return ROTGP_EINVAL;
+  ++c->plan_version;
   if (axis < 0 || axis >= c->grid.dim) return fail(c, ROTGP_EINVAL, "axis out of range");
   if (solver != ROTGP_SOLVER_THOMAS && solver != ROTGP_SOLVER_STENCIL &&
       solver != ROTGP_SOLVER_FUSED)
@@ -1189,6 +1199,7 @@ int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
 
 int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
   if (!c) return ROTGP_EINVAL;
+  ++c->plan_version;
   if (steps < 1) return fail(c, ROTGP_EINVAL, "steps must be >= 1");
   const int dim = c->grid.dim;
   // candidate forms: bit a = axis a in stencil form, bit 3 = fused x-y pass

@@ -59,7 +59,7 @@ class Phys(ctypes.Structure):
 class Obs(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("norm", "mu", "energy", "mu_c", "energy_c",
                                                 "rms_x", "rms_y", "rms_z", "rms_r",
-                                                "max_density")] + \
+                                                "max_density", "mu4", "energy4")] + \
                [("step", ctypes.c_longlong), ("vortices", ctypes.c_int), ("flags", ctypes.c_int)]
 
     def as_dict(self) -> dict:

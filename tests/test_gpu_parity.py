@@ -19,7 +19,7 @@ from paper_1906_06327_gb300.rotgp import (ROTGP_EINVAL, ROTGP_ENONFINITE, ROTGP_
 
 pytestmark = pytest.mark.gpu
 
-OBS_REL = ("mu", "energy", "mu_c", "energy_c")
+OBS_REL = ("mu", "energy", "mu_c", "energy_c", "mu4", "energy4")
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -393,3 +393,47 @@ def test_vortex_count_on_constructed_states(fp32):
                           [(0.55, 0.5), (-0.6, -0.4)], [1, 1])
     psi3 = np.repeat(plane[None, :, :], 9, axis=0)
     assert oracle.vortex_count(g3, psi3, fp32) == 2
+
+
+# ------------------------------------------------- fourth-order energies
+def _analytic_energies(n, h, function, omega):
+    grid = Grid((n, n), (h, h))
+    phys = Phys(gamma=1.0, nu=1.0, g=0.0, omega=omega, dt=1e-3)
+    psi = oracle.init_analytic(grid, function, None)
+    return oracle.observables(grid, phys, psi)
+
+
+def test_fourth_order_energy_of_gaussian_is_exact_to_h4():
+    """The isotropic harmonic ground state exp(-r^2/2)/sqrt(pi) has E = mu = 1
+    (g = 0, Omega = 0).  With fourth-order differences the grid error is
+    O(h^4): far below the O(h^2) error of the three-point forms, and it falls
+    by ~16 when h halves (a wrong stencil coefficient breaks both)."""
+    ob = _analytic_energies(128, 0.1, 0, 0.0)
+    e4, e2 = abs(ob["energy4"] - 1.0), abs(ob["energy_c"] - 1.0)
+    assert e4 < 3e-6 and e2 > 20 * e4, (e4, e2)
+    assert abs(ob["mu4"] - ob["energy4"]) < 1e-13
+    coarse = abs(_analytic_energies(64, 0.2, 0, 0.0)["energy4"] - 1.0)
+    assert 12.0 < coarse / e4 < 20.0, coarse / e4
+
+
+def test_fourth_order_energy_of_one_vortex_is_two_minus_omega():
+    """(x + i y) exp(-r^2/2) is an L_z = +1 eigenstate with E = 2 - Omega
+    (g = 0); the fourth-order evaluation includes the rotation term
+    -Omega L_z through the fourth-order first derivatives."""
+    omega = 0.5
+    ob = _analytic_energies(128, 0.1, 1, omega)
+    e4, e2 = abs(ob["energy4"] - (2 - omega)), abs(ob["energy_c"] - (2 - omega))
+    assert e4 < 2e-5 and e2 > 20 * e4, (e4, e2)
+    coarse = abs(_analytic_energies(64, 0.2, 1, omega)["energy4"] - (2 - omega))
+    assert 12.0 < coarse / e4 < 20.0, coarse / e4
+
+
+def test_fourth_order_forms_share_the_interaction_term():
+    """mu - E is the interaction energy (g/2) sum |psi|^4 / sum |psi|^2 in
+    both the three-point and the fourth-order complex forms."""
+    n = (40, 36)
+    grid = Grid(n, (0.3, 0.3))
+    phys = Phys(gamma=1.0, nu=1.1, g=80.0, omega=0.6, dt=1e-3)
+    psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(n[0], n[1], 4))
+    ob = oracle.observables(grid, phys, psi)
+    assert abs((ob["mu4"] - ob["energy4"]) - (ob["mu_c"] - ob["energy_c"])) < 1e-12

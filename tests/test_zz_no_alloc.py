@@ -18,7 +18,7 @@ from paper_1906_06327_gb300 import rotgp
 pytestmark = pytest.mark.gpu
 
 KEYS = ("norm", "mu", "energy", "mu_c", "energy_c", "rms_x", "rms_y", "rms_z", "rms_r",
-        "max_density")
+        "max_density", "mu4", "energy4")
 
 
 @pytest.mark.parametrize("n,h,precision,tol", [

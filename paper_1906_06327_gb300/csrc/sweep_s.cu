@@ -223,14 +223,16 @@ __device__ __forceinline__ void strided_forward2(float4* s0, c2& pm, c2& d,
   for (int r = 0; r < C; ++r) s0[r * 32] = w[r];
 }
 
-template <int C, bool REDUCE>
+// RING: slots of the chunk ring (3 or 4), a compile-time constant so that
+// slot indices are cheap.
+template <int C, bool REDUCE, int RING>
 __global__ void __launch_bounds__(128) k_sweep_strided2(const stream_args a) {
   using E = cpx<float>;
   constexpr int SLOT = (C + 1) * 32;  // float4 (two complex) per slot
+  constexpr int R = RING;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int R = a.ring;
-  if (R < 3 || R > 4 ||
+  if (a.ring != R ||
       dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT) * 16u) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
@@ -276,7 +278,10 @@ __global__ void __launch_bounds__(128) k_sweep_strided2(const stream_args a) {
     c2 pm = zero2(), d = zero2();
     for (int q = qa; q <= qb; ++q) {
       if (q < qb) {
-        ring_wait(R);
+        if (R == 3)
+          cp_async_wait<1>();
+        else
+          cp_async_wait<2>();
         if (q * C >= lt && (q + 1) * C <= N)
           strided_forward2<C, true>(slot(q), pm, d, crow, cf, q * C, lt);
         else
@@ -288,7 +293,9 @@ __global__ void __launch_bounds__(128) k_sweep_strided2(const stream_args a) {
         const int la = min(a.halo, N - q * C);
         const float4* sq = slot(q);
         const bool la_fast = q * C >= lt;
-        for (int h = la - 1; h >= 0; --h) {
+#pragma unroll
+        for (int h = C - 1; h >= 0; --h) {
+          if (h >= la) continue;  // the halo is at most one chunk
           k2 be = cf.be;
           if (!la_fast) {
             const int i = min(q * C + h, lt);
@@ -379,9 +386,11 @@ static cudaError_t dispatch_s(bool reduce, const stream_args& a, const sweep_sha
 template <int C>
 static cudaError_t dispatch_s2(bool reduce, const stream_args& a, const sweep_shape& sh,
                                cudaStream_t s) {
-  static bool done[2] = {false, false};
-  auto fn = reduce ? k_sweep_strided2<C, true> : k_sweep_strided2<C, false>;
-  cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
+  static bool done[4] = {false, false, false, false};
+  if (sh.R != 3 && sh.R != 4) return cudaErrorInvalidValue;
+  auto fn = sh.R == 3 ? (reduce ? k_sweep_strided2<C, true, 3> : k_sweep_strided2<C, false, 3>)
+                      : (reduce ? k_sweep_strided2<C, true, 4> : k_sweep_strided2<C, false, 4>);
+  cudaError_t e = allow_smem((const void*)fn, &done[(sh.R == 4 ? 2 : 0) + (reduce ? 1 : 0)]);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
   return cudaGetLastError();

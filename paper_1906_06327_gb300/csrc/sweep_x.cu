@@ -235,10 +235,11 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
 // TMA = true: each chunk (64 rows x C + 2 points, exactly a ring slot) is
 // one 2-D TMA box issued by lane 0 on a per-slot barrier, instead of the
 // lanes' cooperative copies (needs 16-byte rows, VEC16).
-template <int C, bool IMAG, bool VEC16, bool TMA>
+template <int C, bool IMAG, bool VEC16, bool TMA, int RING>
 __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtensorMap map,
                                                   const stream_args a) {
   using E = cpx<float>;
+  constexpr int R = RING;  // ring slots (3 or 4), compile-time for cheap slot indices
   constexpr int EP = VEC16 ? 2 : 1;
   constexpr int PITCH = C + 2;                 // odd number of 16-byte units
   constexpr int ROWS = 64;
@@ -250,9 +251,8 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[TMA ? 4 * 4 : 1];  // [warp][slot]
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int R = a.ring;
   const unsigned pad = TMA ? 128 : 0;  // TMA destinations start on 128 bytes
-  if (R < 3 || R > 4 || (TMA && blockDim.x > 128) ||
+  if (a.ring != R || (TMA && blockDim.x > 128) ||
       dynamic_smem_bytes() <
           (blockDim.x >> 5) * (unsigned)(R * SLOT) * (unsigned)sizeof(E) + pad) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
@@ -416,8 +416,10 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
           if (lane == 0) atomicOr(a.flags, 4);
           return;
         }
+      } else if (R == 3) {
+        cp_async_wait<1>();
       } else {
-        ring_wait(R);
+        cp_async_wait<2>();
       }
       __syncwarp();
       if (q * C >= lt && (q + 1) * C <= N)
@@ -469,21 +471,31 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
   if (!TMA) cp_async_wait<0>();
 }
 
-template <int C>
-static cudaError_t dispatch_x2(bool imag, bool vec16, const stream_args& a, const sweep_shape& sh,
-                               const void* map, cudaStream_t s) {
+template <int C, int R>
+static cudaError_t dispatch_x2r(bool imag, bool vec16, const stream_args& a,
+                                const sweep_shape& sh, const void* map, cudaStream_t s) {
   static bool done[6] = {false, false, false, false, false, false};
   const bool tma = map != nullptr && vec16 && sh.warps_per_block <= 4;
   static const CUtensorMap none{};
   const CUtensorMap& m = tma ? *static_cast<const CUtensorMap*>(map) : none;
-  auto fn = tma ? (imag ? k_sweep_x2<C, true, true, true> : k_sweep_x2<C, false, true, true>)
-          : vec16 ? (imag ? k_sweep_x2<C, true, true, false> : k_sweep_x2<C, false, true, false>)
-                  : (imag ? k_sweep_x2<C, true, false, false> : k_sweep_x2<C, false, false, false>);
+  auto fn = tma ? (imag ? k_sweep_x2<C, true, true, true, R> : k_sweep_x2<C, false, true, true, R>)
+          : vec16 ? (imag ? k_sweep_x2<C, true, true, false, R>
+                          : k_sweep_x2<C, false, true, false, R>)
+                  : (imag ? k_sweep_x2<C, true, false, false, R>
+                          : k_sweep_x2<C, false, false, false, R>);
   const int k = (tma ? 4 : vec16 ? 2 : 0) + (imag ? 1 : 0);
   cudaError_t e = allow_smem((const void*)fn, &done[k]);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem + (tma ? 128 : 0), s>>>(m, a);
   return cudaGetLastError();
+}
+
+template <int C>
+static cudaError_t dispatch_x2(bool imag, bool vec16, const stream_args& a, const sweep_shape& sh,
+                               const void* map, cudaStream_t s) {
+  if (sh.R == 3) return dispatch_x2r<C, 3>(imag, vec16, a, sh, map, s);
+  if (sh.R == 4) return dispatch_x2r<C, 4>(imag, vec16, a, sh, map, s);
+  return cudaErrorInvalidValue;
 }
 
 template <class T, int V, int C>

@@ -160,13 +160,24 @@ __global__ void __launch_bounds__(kThreads) k_observables_noalloc(
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // every thread sums a fixed strided subset of the blocks, then the warps
+  // and the block combine in a fixed order (deterministic)
   __shared__ double fin[NQ];
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) {
+    double s = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += kThreads) {
+      const double x = __ldcg(&partials[(size_t)b * NQ + v]);
+      s = v == NQ - 1 ? fmax(s, x) : s + x;
+    }
+    s = v == NQ - 1 ? nmax(s) : nsum(s);
+    if (lane == 0) ws[warp][v] = s;
+  }
+  __syncthreads();
   if (threadIdx.x < NQ) {
     double s = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-      const double x = __ldcg(&partials[(size_t)b * NQ + threadIdx.x]);
-      s = threadIdx.x == NQ - 1 ? fmax(s, x) : s + x;
-    }
+    for (int w = 0; w < kThreads / 32; ++w)
+      s = threadIdx.x == NQ - 1 ? fmax(s, ws[w][threadIdx.x]) : s + ws[w][threadIdx.x];
     fin[threadIdx.x] = s;
   }
   __syncthreads();

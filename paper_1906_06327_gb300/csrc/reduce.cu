@@ -54,14 +54,33 @@ __device__ bool block_partials(double* q, double* partials, unsigned* counter) {
 }
 
 // In the last block: thread v < NV sums partial v over all blocks in order.
+// Combine the partials of all blocks into fin[0..NV) (shared), in the last
+// block: thread t sums blocks t, t + blockDim, ... in order, then warps and
+// the block reduce in a fixed order (deterministic run to run).  Every
+// thread of the block must call it.
 template <int NV, bool MAXLAST>
-__device__ double combine(const double* partials, int v) {
-  double s = 0;
-  for (unsigned b = 0; b < gridDim.x; ++b) {
-    const double x = __ldcg(&partials[(size_t)b * NV + v]);
-    s = (MAXLAST && v == NV - 1) ? fmax(s, x) : s + x;
+__device__ void combine_all(const double* partials, double* fin) {
+  __shared__ double red[32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const bool mx = MAXLAST && v == NV - 1;
+    double s = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+      const double x = __ldcg(&partials[(size_t)b * NV + v]);
+      s = mx ? fmax(s, x) : s + x;
+    }
+    s = mx ? wmax(s) : wsum(s);
+    if (lane == 0) red[warp][v] = s;
   }
-  return s;
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const bool mx = MAXLAST && (int)threadIdx.x == NV - 1;
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s = mx ? fmax(s, red[w][threadIdx.x]) : s + red[w][threadIdx.x];
+    fin[threadIdx.x] = s;
+  }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------ observables
@@ -168,8 +187,7 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
   if (!block_partials<NQ, true>(q, a.partials, a.counter)) return;
   __shared__ double fin[NQ];
   __threadfence();
-  if (threadIdx.x < NQ) fin[threadIdx.x] = combine<NQ, true>(a.partials, threadIdx.x);
-  __syncthreads();
+  combine_all<NQ, true>(a.partials, fin);
   if (threadIdx.x == 0) {
     double vol = a.hx * a.hy * (a.dim == 3 ? a.hz : 1.0);
     const bool rot = fin[1] < 1e-3 * fin[0];
@@ -214,8 +232,7 @@ __global__ void __launch_bounds__(256) k_vort_moments(const vort_args a) {
   if (!block_partials<3, false>(q, a.partials, a.counter)) return;
   __shared__ double fin[3];
   __threadfence();
-  if (threadIdx.x < 3) fin[threadIdx.x] = combine<3, false>(a.partials, threadIdx.x);
-  __syncthreads();
+  combine_all<3, false>(a.partials, fin);
   if (threadIdx.x == 0) {
     a.moments[0] = fin[0] > 0 ? 6.0 * fin[1] / fin[0] : 0.0;
     a.moments[1] = fin[0] > 0 ? 6.0 * fin[2] / fin[0] : 0.0;
@@ -278,8 +295,10 @@ __global__ void __launch_bounds__(256) k_norm(const void* psi_v, long long n, do
     q[0] += (double)abs2(psi[idx]);
   if (!block_partials<1, false>(q, partials, counter)) return;
   __threadfence();
+  __shared__ double fin1[1];
+  combine_all<1, false>(partials, fin1);
   if (threadIdx.x == 0) {
-    const double nrm = combine<1, false>(partials, 0) * vol;
+    const double nrm = fin1[0] * vol;
     *norm_out = nrm;
     if (!(nrm > 0.0) || !isfinite(nrm)) {
       atomicOr(flags, 1);

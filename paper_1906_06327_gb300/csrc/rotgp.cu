@@ -1285,7 +1285,8 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
         for (int C : {8, 16, 64})
           for (int R : {3, 4}) shapes.push_back({C, R, keep.nseg});
       } else {
-        for (int sg : {1, 2, 3, 4, 6, 8, 12, 16}) shapes.push_back({keep.sh.C, keep.sh.R, sg});
+        for (int sg : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
+          shapes.push_back({keep.sh.C, keep.sh.R, sg});
       }
       for (const auto& sh : shapes) {
         if (sh[0] == keep.sh.C && sh[1] == keep.sh.R && sh[2] == keep.nseg) continue;

@@ -180,6 +180,11 @@ inline bool stencil_k_built(int K) { return K == 4 || K == 6 || K == 8; }
 bool tile_k_built(int K);
 unsigned xy_pass_smem(int K);  // dynamic shared memory of one xy-pass CTA
 int xy_pass_ctas_per_sm(int K, bool imag, bool reduce);  // resident CTAs per SM
+// x sweep alone in stencil form (tiles of 32 rows x 64 points): map with box
+// {2 (64 + 2K + 2), 32, 1}
+int x_pass_ctas_per_sm(int K);
+cudaError_t launch_x_pass(bool imag, int K, const void* map, const tile_args& a, unsigned blocks,
+                          cudaStream_t s);
 void xy_tile_geometry(int K, int* TX, int* TY, int* R, int* WX);
 int line_rows();
 cudaError_t launch_xy_pass(bool imag, bool reduce, int K, const void* map, const tile_args& a,

@@ -88,6 +88,8 @@ struct rotgp_ctx {
   bool x_tma = true;  // Thomas x sweep loads its chunks with TMA (when the maps exist)
   long long plan_version = 0;  // bumped whenever launches or tables change
   CUtensorMap map_xy[2], map_y[2], map_z[2];
+  bool xpass_ok = false;  // x sweep alone in stencil form through TMA tiles
+  CUtensorMap map_xp[2];
   // rows maps of the Thomas x sweep's TMA chunk loads: [buffer][C = 8, 16]
   bool xmaps_ok = false;
   CUtensorMap map_x[2][2];
@@ -402,6 +404,17 @@ void xy_shape(const rotgp_ctx* c, int* tiles_x, int* tiles_y, int* zchunk, unsig
   *zchunk = (c->nz + chunks - 1) / chunks;
   *blocks = (unsigned)(txy * ((c->nz + *zchunk - 1) / *zchunk));
 }
+// Launch shape of the x pass: as the xy pass, tiles of 32 rows x 64 points.
+void x_shape(const rotgp_ctx* c, int* tiles_x, int* tiles_y, int* zchunk, unsigned* blocks) {
+  *tiles_x = (c->nx + 63) / 64;
+  *tiles_y = (c->ny + 31) / 32;
+  const long long txy = (long long)*tiles_x * *tiles_y;
+  const long long resident = (long long)x_pass_ctas_per_sm(c->axis[0].sK) * c->sm_count;
+  const int chunks = (int)std::max<long long>(1, std::min<long long>(c->nz, resident / txy));
+  *zchunk = (c->nz + chunks - 1) / chunks;
+  *blocks = (unsigned)(txy * ((c->nz + *zchunk - 1) / *zchunk));
+}
+
 unsigned xy_blocks(const rotgp_ctx* c) {
   int tx, ty, zc;
   unsigned b;
@@ -451,6 +464,11 @@ void build_maps(rotgp_ctx* c) {
     ok = ok && encode_state_map(&c->map_y[b], c->psi[b], c->nx, c->ny, c->nz, 64, 8, rows) == 0;
     ok = ok && encode_state_map(&c->map_z[b], c->psi[b], c->nx, c->ny, c->nz, 64, rows, 8) == 0;
   }
+  // the x sweep alone in stencil form: boxes of 32 rows x (64 + 2K + 2) points
+  c->xpass_ok = !c->fp64 && c->nx % 2 == 0 && c->axis[0].stencil_ok && tile_k_built(c->axis[0].sK);
+  for (int b = 0; b < 2 && c->xpass_ok; ++b)
+    c->xpass_ok = encode_state_map(&c->map_xp[b], c->psi[b], c->nx, c->ny, c->nz,
+                                   2 * (64 + 2 * c->axis[0].sK + 2), 32, 1) == 0;
   // the Thomas x sweep: boxes of 64 rows x (C + 2) points
   c->xmaps_ok = !c->fp64 && c->nx % 2 == 0;
   for (int b = 0; b < 2 && c->xmaps_ok; ++b)
@@ -618,7 +636,12 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
     a.scale = c->d_scale();
     Timed t(c, K_SWEEP_X);
-    if (ap.use_stencil && imag && c->nx % 4 == 0) {
+    if (ap.use_stencil && imag && c->xpass_ok) {
+      tile_args ta = make_tile_args(c, imag);
+      unsigned blocks;
+      x_shape(c, &ta.tiles_x, &ta.tiles_y, &ta.zchunk, &blocks);
+      e = launch_x_pass(imag, ap.sK, &c->map_xp[c->cur], ta, blocks, c->stream);
+    } else if (ap.use_stencil && imag && c->nx % 4 == 0) {
       const long long warps = ((ap.lines + 1) / 2) * ((ap.len + 127) / 128);
       e = launch_stencil_x(imag, a, warps, c->stream);
     } else {
@@ -1190,7 +1213,8 @@ int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
     c->fuse_xy = true;
     return ROTGP_OK;
   }
-  if (solver == ROTGP_SOLVER_STENCIL && (!ap.stencil_ok || (axis == 0 && c->nx % 4 != 0)))
+  if (solver == ROTGP_SOLVER_STENCIL &&
+      (!ap.stencil_ok || (axis == 0 && c->nx % 4 != 0 && !c->xpass_ok)))
     return fail(c, ROTGP_EUNSUPPORTED, "no stencil form for axis %d of this context", axis);
   ap.use_stencil = solver == ROTGP_SOLVER_STENCIL;
   if (axis <= 1) c->fuse_xy = false;
@@ -1207,7 +1231,8 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
   for (int m = 0; m < (1 << dim); ++m) {
     bool ok = true;
     for (int a = 0; a < dim; ++a)
-      if ((m >> a) & 1) ok = ok && c->axis[a].stencil_ok && (a != 0 || c->nx % 4 == 0);
+      if ((m >> a) & 1)
+        ok = ok && c->axis[a].stencil_ok && (a != 0 || c->nx % 4 == 0 || c->xpass_ok);
     if (ok) cand.push_back(m);
   }
   if (c->fuse_ok) {

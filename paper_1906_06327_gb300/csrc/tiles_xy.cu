@@ -256,6 +256,145 @@ __global__ void __launch_bounds__(128) k_xy_pass(const __grid_constant__ CUtenso
   if (REDUCE) norm_epilogue(acc.value(), a);
 }
 
+// ------------------------------------------------------------ x sweep alone
+// The x sweep (with the pending scale and H1) in stencil form when the y
+// sweep is not fused with it: tiles of 32 rows x 64 points of one plane
+// with the K-point x halo, staged by one TMA load (double-buffered along
+// the CTA's z range); lane = row, warp = strip of 16 outputs, H1 applied to
+// the strip's window in registers; the results are written back into the
+// staged tile and copied out row by row (coalesced).  No y halo rows.
+template <int K>
+struct x_geom {
+  static constexpr int TX = 64, ROWS = 32;
+  static constexpr int WX = TX + 2 * K + 2;  // complex per staged row (+2: banks)
+  static constexpr unsigned BYTES = (unsigned)(ROWS * WX * 8);
+  static constexpr unsigned SMEM = 2 * BYTES + 128;
+  static_assert(K % 2 == 0 && BYTES % 128 == 0, "x tile geometry");
+};
+
+template <int K, bool IMAG>
+__global__ void __launch_bounds__(128) k_x_pass(const __grid_constant__ CUtensorMap map,
+                                                const tile_args a) {
+  using G = x_geom<K>;
+  constexpr int S = 2 * K + 1;
+  constexpr int XS = 16;
+  constexpr int NWIN = XS + 2 * K;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  unsigned char* base = dsm + ((128 - (smem_addr(dsm) & 127)) & 127);
+  auto raw = [&](int bf) { return reinterpret_cast<float2*>(base + bf * G::BYTES); };
+  __shared__ __align__(8) uint64_t bar[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tiles_xy = a.tiles_x * a.tiles_y;
+  const int txy = blockIdx.x % tiles_xy;
+  const int zb = (blockIdx.x / tiles_xy) * a.zchunk;
+  const int ze = min(a.nz, zb + a.zchunk);
+  const int x0 = (txy % a.tiles_x) * G::TX, y0 = (txy / a.tiles_x) * G::ROWS;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int z, int bf) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[bf], G::BYTES);
+    tma_load_3d(raw(bf), &map, 2 * (x0 - K), y0, z, &bar[bf]);
+  };
+  if (tid == 0 && zb < ze) issue(zb, 0);
+  const int y = y0 + lane;
+  const float2* wxl = static_cast<const float2*>(a.wx) +
+                      (size_t)min(y, a.ny - 1) * (2 * a.bx + 1) * S;
+  float2 XR[S], XI[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) wsplit(wxl[a.bx * S + t], XR[t], XI[t]);
+  const int xq0 = x0 + XS * warp;
+  const bool x_fast = xq0 >= a.bx && xq0 + XS - 1 < a.nx - a.bx;
+  const float yc = a.y0 + (float)y * a.hy;
+  const float vy = a.hnu2 * yc * yc;
+  const float xw = a.x0 + (float)(xq0 - K) * a.hx;
+  const float sc = (float)(*a.scale);
+  bool good = true;
+  int k = 0;
+  for (int z = zb; z < ze; ++k, ++z) {
+    const int bf = k & 1;
+    if (!__syncthreads_and(mbar_wait(&bar[bf], (k >> 1) & 1))) {
+      good = false;
+      break;
+    }
+    // prefetch the next plane into the other buffer: its last reader (the
+    // copy-out of the previous plane) finished before the barrier above
+    if (tid == 0 && z + 1 < ze) issue(z + 1, bf ^ 1);
+    const float zc = a.z0 + (float)z * a.hz;
+    const float vyz = fmaf(a.hlam2, zc * zc, vy);
+    const float4* src = reinterpret_cast<const float4*>(raw(bf) + lane * G::WX + XS * warp);
+    float2 v[NWIN];
+#pragma unroll
+    for (int i = 0; i < NWIN / 2; ++i) {
+      const float4 q = src[i];
+      v[2 * i] = make_float2(q.x, q.y);
+      v[2 * i + 1] = make_float2(q.z, q.w);
+    }
+#pragma unroll
+    for (int t = 0; t < NWIN; ++t) {
+      const float xc = fmaf((float)t, a.hx, xw);
+      v[t] = h1_point<IMAG>(v[t], sc, fmaf(a.hgam2, xc * xc, vyz), a.g, a.dt);
+    }
+    float4 res[XS / 2];
+#pragma unroll
+    for (int m = 0; m < XS; m += 2) {
+      float2 o[2];
+      if (x_fast) {
+        cacc c0 = cacc_zero(), c1 = cacc_zero();
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          cmac(c0, XR[t], XI[t], v[m + t]);
+          cmac(c1, XR[t], XI[t], v[m + 1 + t]);
+        }
+        o[0] = cfin(c0);
+        o[1] = cfin(c1);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int xo_ = xq0 + m + e;
+          const float2* wr = wxl + stencil_row(min(xo_, a.nx - 1), a.nx, a.bx) * S;
+          cacc c = cacc_zero();
+#pragma unroll
+          for (int t = 0; t < S; ++t) {
+            float2 pr, pi;
+            wsplit(wr[t], pr, pi);
+            cmac(c, pr, pi, v[m + e + t]);
+          }
+          o[e] = cfin(c);
+        }
+      }
+      res[m / 2] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    }
+    // every warp has read its window: the results go into the tile's
+    // interior (row pitch WX, conflict-free for lane = row), and the whole
+    // tile is then copied out row by row (32 lanes = 512 contiguous bytes)
+    __syncthreads();
+    {
+      float4* dst = reinterpret_cast<float4*>(raw(bf) + lane * G::WX + K + XS * warp);
+#pragma unroll
+      for (int i = 0; i < XS / 2; ++i) dst[i] = res[i];
+    }
+    __syncthreads();
+    {
+      constexpr int PR = G::TX / 2;  // float4 (two points) per output row
+      float2* outp = static_cast<float2*>(a.out) + (size_t)z * a.ny * a.nx;
+#pragma unroll
+      for (int i = 0; i < G::ROWS * PR / 128; ++i) {
+        const int t = i * 128 + tid, rr = t / PR, cc = t % PR;
+        const int yy = y0 + rr, xx = x0 + 2 * cc;
+        if (yy < a.ny && xx < a.nx)
+          *reinterpret_cast<float4*>(outp + (size_t)yy * a.nx + xx) =
+              *reinterpret_cast<const float4*>(raw(bf) + rr * G::WX + K + 2 * cc);
+      }
+    }
+  }
+  if (!good && tid == 0) atomicOr(a.flags, 4);  // no prefetch was issued for this plane
+}
+
 bool tile_k_built(int K) { return K == 4 || K == 6 || K == 8; }
 
 void xy_tile_geometry(int K, int* TX, int* TY, int* R, int* WX) {
@@ -308,6 +447,50 @@ cudaError_t launch_xy_k(const CUtensorMap& m, const tile_args& a, unsigned block
   if (e != cudaSuccess) return e;
   k_xy_pass<K, IMAG, REDUCE><<<blocks, 128, G::SMEM, s>>>(m, a);
   return cudaGetLastError();
+}
+
+template <int K, bool IMAG>
+cudaError_t x_allow_smem() {
+  static const cudaError_t e = cudaFuncSetAttribute(
+      k_x_pass<K, IMAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x_geom<K>::SMEM);
+  return e;
+}
+
+int x_pass_ctas_per_sm(int K) {
+  int n = 0;
+#define ROTGP_XC(KK)                                                                     \
+  if (K == KK) {                                                                         \
+    if (x_allow_smem<KK, false>() != cudaSuccess ||                                      \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_x_pass<KK, false>, 128,      \
+                                                      x_geom<KK>::SMEM) != cudaSuccess)  \
+      return 1;                                                                          \
+    return n > 0 ? n : 1;                                                                \
+  }
+  ROTGP_XC(4)
+  ROTGP_XC(6)
+  ROTGP_XC(8)
+#undef ROTGP_XC
+  return 1;
+}
+
+cudaError_t launch_x_pass(bool imag, int K, const void* map, const tile_args& a, unsigned blocks,
+                          cudaStream_t s) {
+  const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
+#define ROTGP_XP(KK)                                                                   \
+  if (K == KK) {                                                                       \
+    cudaError_t e = imag ? x_allow_smem<KK, true>() : x_allow_smem<KK, false>();       \
+    if (e != cudaSuccess) return e;                                                    \
+    if (imag)                                                                          \
+      k_x_pass<KK, true><<<blocks, 128, x_geom<KK>::SMEM, s>>>(m, a);                  \
+    else                                                                               \
+      k_x_pass<KK, false><<<blocks, 128, x_geom<KK>::SMEM, s>>>(m, a);                 \
+    return cudaGetLastError();                                                         \
+  }
+  ROTGP_XP(4)
+  ROTGP_XP(6)
+  ROTGP_XP(8)
+#undef ROTGP_XP
+  return cudaErrorInvalidValue;
 }
 
 unsigned xy_pass_smem(int K) {

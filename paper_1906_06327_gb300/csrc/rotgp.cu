@@ -93,6 +93,8 @@ struct rotgp_ctx {
   // rows maps of the Thomas x sweep's TMA chunk loads: [buffer][C = 8, 16]
   bool xmaps_ok = false;
   CUtensorMap map_x[2][2];
+  // ... and of its one-row-per-lane form: boxes of 32 rows, [buffer][C = 8, 16]
+  CUtensorMap map_x1[2][2];
   double* partials = nullptr;
   size_t partial_doubles = 0;
   unsigned* counter = nullptr;
@@ -297,7 +299,10 @@ int set_shape(rotgp_ctx* c, int a, int V, int C, int R, int wpb, long long nseg)
   AxisPlan& ap = c->axis[a];
   const bool x = a == 0;
   const size_t limit = (size_t)c->smem_optin - 1024;
-  if (!sweep_shape_built(c->fp64, V, C))
+  // the x sweep also has a one-row-per-lane TMA form for complex float rows
+  // of 16-byte multiples, chunk 8 or 16
+  const bool x1t = x && !c->fp64 && V == 1 && (C == 8 || C == 16) && c->nx % 2 == 0;
+  if (!sweep_shape_built(c->fp64, V, C) && !x1t)
     return fail(c, ROTGP_EINVAL, "no sweep kernel for %d lines per lane and chunk %d", V, C);
   if (V == 2 && !x && c->nx % 2 != 0)
     return fail(c, ROTGP_EINVAL, "two lines per lane in y/z sweeps need an even N_x");
@@ -475,7 +480,9 @@ void build_maps(rotgp_ctx* c) {
     for (int ci = 0; ci < 2 && c->xmaps_ok; ++ci) {
       const int C = ci == 0 ? 8 : 16;
       c->xmaps_ok = encode_rows_map(&c->map_x[b][ci], c->psi[b], c->nx,
-                                    (long long)c->ny * c->nz, 2 * (C + 2), 64) == 0;
+                                    (long long)c->ny * c->nz, 2 * (C + 2), 64) == 0 &&
+                    encode_rows_map(&c->map_x1[b][ci], c->psi[b], c->nx,
+                                    (long long)c->ny * c->nz, 2 * (C + 2), 32) == 0;
     }
   c->maps_ok = ok;
   if (!ok) {
@@ -646,8 +653,9 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
       e = launch_stencil_x(imag, a, warps, c->stream);
     } else {
       const void* xm = nullptr;
-      if (c->xmaps_ok && c->x_tma && ap.sh.V == 2 && ap.sh.vec16 && (ap.sh.C == 8 || ap.sh.C == 16))
-        xm = &c->map_x[c->cur][ap.sh.C == 8 ? 0 : 1];
+      if (c->xmaps_ok && c->x_tma && ap.sh.vec16 && (ap.sh.C == 8 || ap.sh.C == 16))
+        xm = ap.sh.V == 2 ? &c->map_x[c->cur][ap.sh.C == 8 ? 0 : 1]
+                          : &c->map_x1[c->cur][ap.sh.C == 8 ? 0 : 1];
       e = launch_sweep_x(c->fp64, imag, a, ap.sh, xm, c->stream);
     }
   } else {
@@ -1305,20 +1313,24 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
     for (int phase = 0; phase < 2 && e == cudaSuccess && !rc; ++phase) {
       const AxisPlan keep = ap;
       AxisPlan best_plan = keep;
-      std::vector<std::array<int, 3>> shapes;  // {C, R, segments}
+      std::vector<std::array<int, 4>> shapes;  // {V, C, R, segments}
       if (phase == 0) {
-        for (int C : {8, 16, 64})
-          for (int R : {3, 4}) shapes.push_back({C, R, keep.nseg});
+        for (int V : {1, 2}) {
+          if (V != keep.sh.V && !(ax == 0 && !c->fp64 && c->xmaps_ok)) continue;
+          for (int C : {8, 16, 64})
+            for (int R : {3, 4}) shapes.push_back({V, C, R, keep.nseg});
+        }
       } else {
         for (int sg : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
-          shapes.push_back({keep.sh.C, keep.sh.R, sg});
+          shapes.push_back({keep.sh.V, keep.sh.C, keep.sh.R, sg});
       }
       for (const auto& sh : shapes) {
-        if (sh[0] == keep.sh.C && sh[1] == keep.sh.R && sh[2] == keep.nseg) continue;
-        if (!sweep_shape_built(c->fp64, keep.sh.V, sh[0])) continue;
-        if (set_shape(c, ax, keep.sh.V, sh[0], sh[1], keep.sh.warps_per_block, sh[2]) !=
-                ROTGP_OK ||
-            ap.nseg != sh[2] || ((size_t)ap.sh.blocks > c->partial_doubles && ax == dim - 1)) {
+        if (sh[0] == keep.sh.V && sh[1] == keep.sh.C && sh[2] == keep.sh.R && sh[3] == keep.nseg)
+          continue;
+        const bool x1t = ax == 0 && sh[0] == 1 && (sh[1] == 8 || sh[1] == 16) && c->xmaps_ok;
+        if (!sweep_shape_built(c->fp64, sh[0], sh[1]) && !x1t) continue;
+        if (set_shape(c, ax, sh[0], sh[1], sh[2], keep.sh.warps_per_block, sh[3]) != ROTGP_OK ||
+            ap.nseg != sh[3] || ((size_t)ap.sh.blocks > c->partial_doubles && ax == dim - 1)) {
           ap = keep;
           continue;
         }

@@ -471,6 +471,244 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
   if (!TMA) cp_async_wait<0>();
 }
 
+// One row per lane, complex float, chunks by TMA.  The same folded Thomas
+// recurrences as k_sweep_x2, but each lane keeps its row in the interleaved
+// (re, im) layout in which it is stored: a complex multiply-add with
+// w = wr + i wi is accumulated as A += (wr, wr) * v and B += (wi, wi) * v
+// (packed FP32x2) and finished as (A.x - B.y, A.y + B.x), so no operand is
+// ever re-paired between rows.  32 rows per warp (twice the warps of the
+// two-rows-per-lane form for the same grid).
+template <int C, bool IMAG, int RING>
+__global__ void __launch_bounds__(128) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
+                                                   const stream_args a) {
+  using E = cpx<float>;
+  constexpr int R = RING;
+  constexpr int PITCH = C + 2;  // 16-byte units per row: conflict-free 16-byte loads
+  constexpr int ROWS = 32;
+  constexpr int SLOT = ROWS * PITCH;
+  static_assert((SLOT * 8) % 128 == 0 && C % 2 == 0, "TMA slots");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[4 * 4];  // [warp][slot]
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (a.ring != R || blockDim.x > 128 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT * 8) + 128u) {
+    if (threadIdx.x == 0) atomicOr(a.flags, 2);
+    return;
+  }
+  unsigned char* sbase = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+  float2* ring = reinterpret_cast<float2*>(sbase) + (size_t)wib * R * SLOT;
+  uint64_t* bar = bars + wib * 4;
+  const long long nrows = a.nlines;
+  const long long ngroups = (nrows + ROWS - 1) / ROWS;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (wg >= ngroups * a.nseg) return;  // whole warp; no block barrier below
+  const long long g = wg % ngroups;
+  const int sg = (int)(wg / ngroups);
+  const long long row0 = g * ROWS;
+  const long long row = row0 + lane;
+  const bool act = row < nrows;
+  const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
+  const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
+  const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
+  const int jj = act ? (int)(row % a.ny) : 0, kk = act ? (int)(row / a.ny) : 0;
+  const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) + (size_t)jj * (lt + 1);
+  // the converged coefficients as duplicated pairs
+  float2 A0R, A0I, AMR, AMI, APR, API, ALR, ALI, BER, BEI;
+  {
+    const coef5<float> cf = crow[lt];
+    wsplit(make_float2(cf.a0.x, cf.a0.y), A0R, A0I);
+    wsplit(make_float2(cf.am.x, cf.am.y), AMR, AMI);
+    wsplit(make_float2(cf.ap.x, cf.ap.y), APR, API);
+    wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
+    wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
+  }
+  const float yv = (float)(a.y0 + (double)jj * a.hy), zv = (float)(a.z0 + (double)kk * a.hz);
+  const float vyz = (float)a.hnu2 * yv * yv + (float)a.hlam2 * zv * zv;
+  const float sc = (float)(*a.scale), hg2 = (float)a.hgam2, dt = (float)a.dt, gg = (float)a.g;
+  const float xs = (float)a.x0, hx = (float)a.hx;
+  const float2 SC = make_float2(sc, sc);
+  auto h1 = [&](float2 v, int p) -> float2 {
+    v = __fmul2_rn(SC, v);
+    const float x = fmaf((float)p, hx, xs);
+    const float en = fmaf(gg, fmaf(v.x, v.x, v.y * v.y), fmaf(hg2 * x, x, vyz));
+    if (IMAG) {
+      const float f = __expf(-dt * en);
+      return __fmul2_rn(make_float2(f, f), v);
+    } else {
+      float sn, cs;
+      sincosf(dt * en, &sn, &cs);
+      return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
+    }
+  };
+  // d' = a0 pc + am pm + ap pn + al d' (the d'-dependent products last)
+  auto fwd_fast = [&](float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
+    float2 A = __fmul2_rn(A0R, pc), B = __fmul2_rn(A0I, pc);
+    A = __ffma2_rn(AMR, pm, A);
+    B = __ffma2_rn(AMI, pm, B);
+    A = __ffma2_rn(APR, pn, A);
+    B = __ffma2_rn(API, pn, B);
+    A = __ffma2_rn(ALR, d, A);
+    B = __ffma2_rn(ALI, d, B);
+    return make_float2(A.x - B.y, A.y + B.x);
+  };
+  auto fwd_tab = [&](int p, float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
+    const coef5<float> k = crow[min(p, lt)];
+    cacc c = cacc_zero();
+    float2 wr, wi;
+    wsplit(make_float2(k.a0.x, k.a0.y), wr, wi);
+    cmac(c, wr, wi, pc);
+    wsplit(make_float2(k.am.x, k.am.y), wr, wi);
+    cmac(c, wr, wi, pm);
+    wsplit(make_float2(k.ap.x, k.ap.y), wr, wi);
+    cmac(c, wr, wi, pn);
+    wsplit(make_float2(k.al.x, k.al.y), wr, wi);
+    cmac(c, wr, wi, d);
+    return cfin(c);
+  };
+  // x_p = d'_p + be x_{p+1}
+  auto bstep = [&](float2 br, float2 bi, float2 x, float2 dp) -> float2 {
+    const float2 A = __ffma2_rn(br, x, dp), B = __fmul2_rn(bi, x);
+    return make_float2(A.x - B.y, A.y + B.x);
+  };
+  auto be_at = [&](int p, float2& br, float2& bi) {
+    const coef5<float> k = crow[min(p, lt)];
+    wsplit(make_float2(k.be.x, k.be.y), br, bi);
+  };
+  auto slot = [&](int q) { return ring + (size_t)((q - qa) % R) * SLOT; };
+  auto issue = [&](int q) {
+    if (q < qb && lane == 0) {
+      const int sl = (q - qa) % R;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
+      tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
+    }
+  };
+  if (lane == 0) {
+    for (int i = 0; i < R; ++i) mbar_init(&bar[i], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  for (int i = 0; i < R - 1; ++i) issue(qa + i);
+  float2 pm = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
+  float* out = static_cast<float*>(a.out);
+  for (int q = qa; q <= qb; ++q) {
+    if (q < qb) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&bar[(q - qa) % R], (unsigned)(((q - qa) / R) & 1)))) {
+        for (int r = q + 1; r < min(q + R - 1, qb); ++r)
+          mbar_wait(&bar[(r - qa) % R], (unsigned)(((r - qa) / R) & 1));
+        if (lane == 0) atomicOr(a.flags, 4);
+        return;
+      }
+      // forward over chunk q: stage the row's C + 1 points, advance by H1, solve
+      float2* rp = slot(q) + lane * PITCH;
+      const int p0 = q * C;
+      float2 w[C + 1];
+#pragma unroll
+      for (int i = 0; i < C / 2; ++i) {
+        const float4 t = reinterpret_cast<const float4*>(rp)[i];
+        w[2 * i] = make_float2(t.x, t.y);
+        w[2 * i + 1] = make_float2(t.z, t.w);
+      }
+      w[C] = rp[C];
+#pragma unroll
+      for (int r = 0; r <= C; ++r) w[r] = h1(w[r], p0 + r);
+      if (p0 >= lt && p0 + C <= N) {
+#pragma unroll
+        for (int r = 0; r < C; ++r) {
+          const float2 pc = w[r];
+          d = fwd_fast(pm, pc, w[r + 1], d);
+          pm = pc;
+          w[r] = d;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < C; ++r) {
+          const float2 pc = w[r];
+          d = fwd_tab(p0 + r, pm, pc, w[r + 1], d);
+          pm = pc;
+          w[r] = d;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < C / 2; ++i)
+        reinterpret_cast<float4*>(rp)[i] = make_float4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x,
+                                                        w[2 * i + 1].y);
+    }
+    const int qq = q - 1;
+    if (qq >= qo0 && qq < qo1) {
+      // back substitution: start H points into chunk q from x = 0
+      float2 x = make_float2(0.f, 0.f);
+      const int la = min(a.halo, N - q * C);
+      const float2* sq = slot(q) + lane * PITCH;
+      const bool la_fast = q * C >= lt;
+#pragma unroll
+      for (int h = C - 1; h >= 0; --h) {
+        if (h >= la) continue;  // the halo is at most one chunk
+        float2 br = BER, bi = BEI;
+        if (!la_fast) be_at(q * C + h, br, bi);
+        x = bstep(br, bi, x, sq[h]);
+      }
+      float2* sp = slot(qq) + lane * PITCH;
+      const int p0 = qq * C;
+      float2 w[C];
+#pragma unroll
+      for (int i = 0; i < C / 2; ++i) {
+        const float4 t = reinterpret_cast<const float4*>(sp)[i];
+        w[2 * i] = make_float2(t.x, t.y);
+        w[2 * i + 1] = make_float2(t.z, t.w);
+      }
+      if (p0 >= lt && q * C <= N) {
+#pragma unroll
+        for (int r = C - 1; r >= 0; --r) {
+          x = bstep(BER, BEI, x, w[r]);
+          w[r] = x;
+        }
+      } else {
+#pragma unroll
+        for (int r = C - 1; r >= 0; --r) {
+          if (p0 + r < N) {
+            float2 br, bi;
+            be_at(p0 + r, br, bi);
+            x = bstep(br, bi, x, w[r]);
+          }
+          w[r] = x;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < C / 2; ++i)
+        reinterpret_cast<float4*>(sp)[i] = make_float4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x,
+                                                        w[2 * i + 1].y);
+      __syncwarp();
+      // copy the chunk out: 16-byte pieces, consecutive lanes along a row
+      const float2* sbase_q = slot(qq);
+#pragma unroll
+      for (int i = 0; i < ROWS * (C / 2) / 32; ++i) {
+        const int t = i * 32 + lane, rr = t / (C / 2), cc = t % (C / 2);
+        const long long orow = row0 + rr;
+        const int p = p0 + 2 * cc;
+        if (orow < nrows && p < N)
+          *reinterpret_cast<float4*>(out + 2 * (orow * N + p)) =
+              *reinterpret_cast<const float4*>(sbase_q + rr * PITCH + 2 * cc);
+      }
+    }
+    __syncwarp();
+    issue(q + R - 1);
+  }
+}
+
+template <int C, int R>
+static cudaError_t dispatch_x1t(bool imag, const stream_args& a, const sweep_shape& sh,
+                                const void* map, cudaStream_t s) {
+  static bool done[2] = {false, false};
+  if (sh.warps_per_block > 4) return cudaErrorInvalidValue;
+  const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
+  auto fn = imag ? k_sweep_x1t<C, true, R> : k_sweep_x1t<C, false, R>;
+  cudaError_t e = allow_smem((const void*)fn, &done[imag ? 1 : 0]);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem + 128, s>>>(m, a);
+  return cudaGetLastError();
+}
+
 template <int C, int R>
 static cudaError_t dispatch_x2r(bool imag, bool vec16, const stream_args& a,
                                 const sweep_shape& sh, const void* map, cudaStream_t s) {
@@ -521,6 +759,13 @@ cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const swe
   }
   if (sh.V == 2 && sh.C == 8) return dispatch_x2<8>(imag, sh.vec16, a, sh, map, s);
   if (sh.V == 2 && sh.C == 16) return dispatch_x2<16>(imag, sh.vec16, a, sh, map, s);
+  // one row per lane through TMA (the host passes the 32-row map)
+  if (sh.V == 1 && (sh.C == 8 || sh.C == 16) && sh.vec16 && map) {
+    if (sh.C == 8) return sh.R == 3 ? dispatch_x1t<8, 3>(imag, a, sh, map, s)
+                                    : dispatch_x1t<8, 4>(imag, a, sh, map, s);
+    return sh.R == 3 ? dispatch_x1t<16, 3>(imag, a, sh, map, s)
+                     : dispatch_x1t<16, 4>(imag, a, sh, map, s);
+  }
   if (sh.V == 1 && sh.C == 16) return dispatch_x<float, 1, 16>(imag, sh.vec16, a, sh, s);
   if (sh.V == 1 && sh.C == 64) return dispatch_x<float, 1, 64>(imag, sh.vec16, a, sh, s);
   return cudaErrorInvalidValue;

@@ -386,3 +386,24 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
     s.init_analytic(1, inputs.random_phase_field(n[0], n[1], 0), 1.0, 1.0)
     s.step_imag(5)
     assert abs(s.observables()["norm"] - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(1, 8, 3, 2), (1, 16, 4, 3), (2, 8, 3, 2), (2, 16, 4, 1)])
+@pytest.mark.parametrize("n,h", [((100, 64), (0.12, 0.15)), ((46, 36, 30), (0.3, 0.3, 0.25))])
+@pytest.mark.parametrize("imag", [True, False])
+def test_thomas_x_launch_shapes_fp32(shape, n, h, imag):
+    """Every launch shape of the Thomas x sweep (one or two rows per lane,
+    chunk, ring, segments) gives the oracle's state after 20 steps up to
+    float rounding."""
+    V, C, R, sg = shape
+    phys = dict(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3)
+    R_ = inputs.random_phase_field(n[0], n[1], 5)
+    s = Solver(n, h, precision="fp32", **phys)
+    s.tune(0, V, C, R, 1, sg)
+    info = s.info()
+    assert (info["lines_per_lane"][0], info["chunk"][0], info["ring"][0]) == (V, C, R)
+    s.init_analytic(1, R_, 1.0, 1.0)
+    (s.step_imag if imag else s.step_real)(20)
+    grid = Grid(n, h)
+    ref, _ = oracle.steps(grid, Phys(**phys), oracle.init_analytic(grid, 1, R_), 20, imag)
+    assert np.max(np.abs(s.get_psi() - ref)) <= 5e-6 * np.max(np.abs(ref))

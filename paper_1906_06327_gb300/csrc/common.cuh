@@ -166,7 +166,10 @@ cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis
 cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,
                            const void* map, cudaStream_t s);  // map: rows TMA map or null
 cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
-                                 const sweep_shape& sh, cudaStream_t s);
+                                 const sweep_shape& sh, const void* map, int axis,
+                                 cudaStream_t s);  // map: one-line-per-lane TMA map or null
+// blocks of the one-line-per-lane strided form with one warp per block
+long long strided1_blocks(long long nlines, int nx, int nseg);
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);
 // banded-inverse stencil form of the complex-float sweeps (stencil.cu)
 cudaError_t launch_stencil_tables(void* wtab, int nlines, int K, int B, int m,

@@ -95,6 +95,10 @@ struct rotgp_ctx {
   CUtensorMap map_x[2][2];
   // ... and of its one-row-per-lane form: boxes of 32 rows, [buffer][C = 8, 16]
   CUtensorMap map_x1[2][2];
+  // one-line-per-lane y/z Thomas sweeps: boxes of 32 lines x (C + 1) positions,
+  // [buffer][axis - 1][C = 8, 16]
+  bool smaps_ok = false;
+  CUtensorMap map_s1[2][2][2];
   double* partials = nullptr;
   size_t partial_doubles = 0;
   unsigned* counter = nullptr;
@@ -301,7 +305,7 @@ int set_shape(rotgp_ctx* c, int a, int V, int C, int R, int wpb, long long nseg)
   const size_t limit = (size_t)c->smem_optin - 1024;
   // the x sweep also has a one-row-per-lane TMA form for complex float rows
   // of 16-byte multiples, chunk 8 or 16
-  const bool x1t = x && !c->fp64 && V == 1 && (C == 8 || C == 16) && c->nx % 2 == 0;
+  const bool x1t = !c->fp64 && V == 1 && (C == 8 || C == 16) && c->nx % 2 == 0;
   if (!sweep_shape_built(c->fp64, V, C) && !x1t)
     return fail(c, ROTGP_EINVAL, "no sweep kernel for %d lines per lane and chunk %d", V, C);
   if (V == 2 && !x && c->nx % 2 != 0)
@@ -469,6 +473,15 @@ void build_maps(rotgp_ctx* c) {
     ok = ok && encode_state_map(&c->map_y[b], c->psi[b], c->nx, c->ny, c->nz, 64, 8, rows) == 0;
     ok = ok && encode_state_map(&c->map_z[b], c->psi[b], c->nx, c->ny, c->nz, 64, rows, 8) == 0;
   }
+  // the y and z Thomas sweeps, one line per lane
+  c->smaps_ok = !c->fp64 && c->nx % 2 == 0;
+  for (int b = 0; b < 2 && c->smaps_ok; ++b)
+    for (int ax = 1; ax < c->grid.dim && c->smaps_ok; ++ax)
+      for (int ci = 0; ci < 2 && c->smaps_ok; ++ci) {
+        const unsigned pts = (ci == 0 ? 8 : 16) + 1;
+        c->smaps_ok = encode_state_map(&c->map_s1[b][ax - 1][ci], c->psi[b], c->nx, c->ny,
+                                       c->nz, 64, ax == 1 ? pts : 1, ax == 1 ? 1 : pts) == 0;
+      }
   // the x sweep alone in stencil form: boxes of 32 rows x (64 + 2K + 2) points
   c->xpass_ok = !c->fp64 && c->nx % 2 == 0 && c->axis[0].stencil_ok && tile_k_built(c->axis[0].sK);
   for (int b = 0; b < 2 && c->xpass_ok; ++b)
@@ -671,7 +684,10 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
       e = launch_line_pass(axis, last, ap.sK, axis == 1 ? &c->map_y[c->cur] : &c->map_z[c->cur],
                            ta, line_blocks(c, axis), c->stream);
     } else {
-      e = launch_sweep_strided(c->fp64, last, a, ap.sh, c->stream);
+      const void* sm = nullptr;
+      if (c->smaps_ok && ap.sh.V == 1 && (ap.sh.C == 8 || ap.sh.C == 16))
+        sm = &c->map_s1[c->cur][axis - 1][ap.sh.C == 8 ? 0 : 1];
+      e = launch_sweep_strided(c->fp64, last, a, ap.sh, sm, axis, c->stream);
     }
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
@@ -855,8 +871,10 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     // largest block count any launch shape of the last sweep can take:
     // one warp per block, one line per lane, one segment per chunk
     const AxisPlan& last = c->axis[grid->dim - 1];
-    const long long nch = (last.len + 15) / 16;
+    const long long nch = (last.len + 7) / 8;
     pd = std::max(pd, (size_t)(((last.lines + 31) / 32) * nch));
+    // the one-line-per-lane form groups lines by 32 consecutive x
+    pd = std::max(pd, (size_t)strided1_blocks(last.lines, c->nx, (int)nch));
   }
   pd = std::max(pd, (size_t)reduce_blocks(c, (long long)c->nx * c->ny) * 3);
   c->partial_doubles = pd;
@@ -1316,7 +1334,8 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
       std::vector<std::array<int, 4>> shapes;  // {V, C, R, segments}
       if (phase == 0) {
         for (int V : {1, 2}) {
-          if (V != keep.sh.V && !(ax == 0 && !c->fp64 && c->xmaps_ok)) continue;
+          const bool lean_ok = !c->fp64 && (ax == 0 ? c->xmaps_ok : c->smaps_ok);
+          if (V != keep.sh.V && !lean_ok) continue;
           for (int C : {8, 16, 64})
             for (int R : {3, 4}) shapes.push_back({V, C, R, keep.nseg});
         }
@@ -1327,7 +1346,8 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
       for (const auto& sh : shapes) {
         if (sh[0] == keep.sh.V && sh[1] == keep.sh.C && sh[2] == keep.sh.R && sh[3] == keep.nseg)
           continue;
-        const bool x1t = ax == 0 && sh[0] == 1 && (sh[1] == 8 || sh[1] == 16) && c->xmaps_ok;
+        const bool x1t = sh[0] == 1 && (sh[1] == 8 || sh[1] == 16) &&
+                         (ax == 0 ? c->xmaps_ok : c->smaps_ok);
         if (!sweep_shape_built(c->fp64, sh[0], sh[1]) && !x1t) continue;
         if (set_shape(c, ax, sh[0], sh[1], sh[2], keep.sh.warps_per_block, sh[3]) != ROTGP_OK ||
             ap.nseg != sh[3] || ((size_t)ap.sh.blocks > c->partial_doubles && ax == dim - 1)) {

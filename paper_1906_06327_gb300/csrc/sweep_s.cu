@@ -9,6 +9,7 @@
 // and stores its results straight to global memory, coalesced.  The solver
 // and the ring are described in sweep_common.cuh.
 #include "sweep_common.cuh"
+#include "tma.cuh"
 
 namespace rotgp {
 
@@ -398,8 +399,216 @@ static cudaError_t dispatch_s2(bool reduce, const stream_args& a, const sweep_sh
 
 // Every (precision, V, C) combination the host can choose is instantiated
 // here; anything else is rejected before a launch.
+// One line per lane, complex float, chunks by TMA (the strided counterpart
+// of k_sweep_x1t).  A warp owns 32 consecutive x of one transverse position
+// (z for y lines, AX = 1; y for z lines, AX = 2): one line position of its
+// 32 lines is 256 contiguous bytes, so each chunk of C + 1 positions is one
+// 3-D TMA box landing as [position][lane] (conflict-free 8-byte shared
+// reads), and every output position is one coalesced 256-byte store straight
+// from registers.  Arithmetic on the interleaved (re, im) layout with two
+// packed-FP32x2 accumulators, as in k_sweep_x1t.
+template <int C, bool REDUCE, int RING, int AX>
+__global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUtensorMap map,
+                                                   const stream_args a) {
+  constexpr int R = RING;
+  constexpr int SLOT = (C + 1) * 32;  // float2 per slot
+  static_assert((SLOT * 8) % 128 == 0, "TMA slots");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[4 * 4];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (a.ring != R || blockDim.x > 128 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT * 8) + 128u) {
+    if (threadIdx.x == 0) atomicOr(a.flags, 2);
+    return;
+  }
+  unsigned char* sbase = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+  float2* ring = reinterpret_cast<float2*>(sbase) + (size_t)wib * R * SLOT;
+  uint64_t* bar = bars + wib * 4;
+  const int tiles_x = (a.nx + 31) / 32;
+  const int nt = (int)(a.nlines / a.nx);  // transverse positions
+  const long long ngroups = (long long)tiles_x * nt;
+  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  acc_t<float> acc;
+  if (wg < ngroups * a.nseg) {
+    const long long g = wg % ngroups;
+    const int sg = (int)(wg / ngroups);
+    const int gx = (int)(g % tiles_x), gt = (int)(g / tiles_x);
+    const int x = 32 * gx + lane;
+    const bool act = x < a.nx;
+    const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
+    const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
+    const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
+    const long long base = (long long)gt * a.outer + x;  // the line's point 0
+    float2* out = static_cast<float2*>(a.out) + (act ? base : 0);
+    const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) +
+                               (size_t)(a.coef_mode == 1 && act ? x : 0) * (lt + 1);
+    float2 A0R, A0I, AMR, AMI, APR, API, ALR, ALI, BER, BEI;
+    {
+      const coef5<float> cf = crow[lt];
+      wsplit(make_float2(cf.a0.x, cf.a0.y), A0R, A0I);
+      wsplit(make_float2(cf.am.x, cf.am.y), AMR, AMI);
+      wsplit(make_float2(cf.ap.x, cf.ap.y), APR, API);
+      wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
+      wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
+    }
+    auto fwd_fast = [&](float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
+      float2 A = __fmul2_rn(A0R, pc), B = __fmul2_rn(A0I, pc);
+      A = __ffma2_rn(AMR, pm, A);
+      B = __ffma2_rn(AMI, pm, B);
+      A = __ffma2_rn(APR, pn, A);
+      B = __ffma2_rn(API, pn, B);
+      A = __ffma2_rn(ALR, d, A);
+      B = __ffma2_rn(ALI, d, B);
+      return make_float2(A.x - B.y, A.y + B.x);
+    };
+    auto fwd_tab = [&](int p, float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
+      const coef5<float> k = crow[min(p, lt)];
+      cacc c = cacc_zero();
+      float2 wr, wi;
+      wsplit(make_float2(k.a0.x, k.a0.y), wr, wi);
+      cmac(c, wr, wi, pc);
+      wsplit(make_float2(k.am.x, k.am.y), wr, wi);
+      cmac(c, wr, wi, pm);
+      wsplit(make_float2(k.ap.x, k.ap.y), wr, wi);
+      cmac(c, wr, wi, pn);
+      wsplit(make_float2(k.al.x, k.al.y), wr, wi);
+      cmac(c, wr, wi, d);
+      return cfin(c);
+    };
+    auto bstep = [&](float2 br, float2 bi, float2 xx, float2 dp) -> float2 {
+      const float2 A = __ffma2_rn(br, xx, dp), B = __fmul2_rn(bi, xx);
+      return make_float2(A.x - B.y, A.y + B.x);
+    };
+    auto be_at = [&](int p, float2& br, float2& bi) {
+      const coef5<float> k = crow[min(p, lt)];
+      wsplit(make_float2(k.be.x, k.be.y), br, bi);
+    };
+    auto slot = [&](int q) { return ring + (size_t)((q - qa) % R) * SLOT + lane; };
+    auto issue = [&](int q) {
+      if (q < qb && lane == 0) {
+        const int sl = (q - qa) % R;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
+        if (AX == 1)
+          tma_load_3d(ring + (size_t)sl * SLOT, &map, 64 * gx, q * C, gt, &bar[sl]);
+        else
+          tma_load_3d(ring + (size_t)sl * SLOT, &map, 64 * gx, gt, q * C, &bar[sl]);
+      }
+    };
+    if (lane == 0) {
+      for (int i = 0; i < R; ++i) mbar_init(&bar[i], 1);
+      mbar_fence_init();
+    }
+    __syncwarp();
+    for (int i = 0; i < R - 1; ++i) issue(qa + i);
+    float2 pm = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
+    bool good = true;
+    for (int q = qa; q <= qb && good; ++q) {
+      if (q < qb) {
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait(&bar[(q - qa) % R], (unsigned)(((q - qa) / R) & 1)))) {
+          for (int r = q + 1; r < min(q + R - 1, qb); ++r)
+            mbar_wait(&bar[(r - qa) % R], (unsigned)(((r - qa) / R) & 1));
+          if (lane == 0) atomicOr(a.flags, 4);
+          good = false;
+          break;
+        }
+        float2* sp = slot(q);
+        const int p0 = q * C;
+        float2 w[C + 1];
+#pragma unroll
+        for (int r = 0; r <= C; ++r) w[r] = sp[r * 32];
+        if (p0 >= lt && p0 + C <= N) {
+#pragma unroll
+          for (int r = 0; r < C; ++r) {
+            const float2 pc = w[r];
+            d = fwd_fast(pm, pc, w[r + 1], d);
+            pm = pc;
+            sp[r * 32] = d;
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < C; ++r) {
+            const float2 pc = w[r];
+            d = fwd_tab(p0 + r, pm, pc, w[r + 1], d);
+            pm = pc;
+            sp[r * 32] = d;
+          }
+        }
+      }
+      const int qq = q - 1;
+      if (qq >= qo0 && qq < qo1) {
+        float2 xx = make_float2(0.f, 0.f);
+        const int la = min(a.halo, N - q * C);
+        const float2* sq = slot(q);
+        const bool la_fast = q * C >= lt;
+#pragma unroll
+        for (int h = C - 1; h >= 0; --h) {
+          if (h >= la) continue;  // the halo is at most one chunk
+          float2 br = BER, bi = BEI;
+          if (!la_fast) be_at(q * C + h, br, bi);
+          xx = bstep(br, bi, xx, sq[h * 32]);
+        }
+        const float2* sp = slot(qq);
+        const int p0 = qq * C;
+        float2 w[C];
+#pragma unroll
+        for (int r = 0; r < C; ++r) w[r] = sp[r * 32];
+        const bool fast = p0 >= lt && q * C <= N;
+#pragma unroll
+        for (int r = C - 1; r >= 0; --r) {
+          const int p = p0 + r;
+          if (!fast && p >= N) continue;
+          float2 br = BER, bi = BEI;
+          if (!fast) be_at(p, br, bi);
+          xx = bstep(br, bi, xx, w[r]);
+          if (act) out[(long long)p * a.stride] = xx;
+          if (REDUCE) acc.add(fmaf(xx.x, xx.x, xx.y * xx.y));
+        }
+      }
+      __syncwarp();
+      issue(q + R - 1);
+    }
+  }
+  if (REDUCE) norm_epilogue(acc.value(), a);
+}
+
+template <int C, int R, int AX>
+static cudaError_t dispatch_s1t(bool reduce, const stream_args& a, const sweep_shape& sh,
+                                const void* map, cudaStream_t s) {
+  static bool done[2] = {false, false};
+  if (sh.warps_per_block > 4) return cudaErrorInvalidValue;
+  const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
+  auto fn = reduce ? k_sweep_s1t<C, true, R, AX> : k_sweep_s1t<C, false, R, AX>;
+  cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
+  if (e != cudaSuccess) return e;
+  const long long groups = (long long)((a.nx + 31) / 32) * (a.nlines / a.nx);
+  const unsigned blocks =
+      (unsigned)((groups * a.nseg + sh.warps_per_block - 1) / sh.warps_per_block);
+  fn<<<blocks, 32 * sh.warps_per_block, sh.smem + 128, s>>>(m, a);
+  return cudaGetLastError();
+}
+
+long long strided1_blocks(long long nlines, int nx, int nseg) {
+  return (long long)((nx + 31) / 32) * (nlines / nx) * nseg;
+}
+
 cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
-                                 const sweep_shape& sh, cudaStream_t s) {
+                                 const sweep_shape& sh, const void* map, int axis,
+                                 cudaStream_t s) {
+  if (!fp64 && sh.V == 1 && (sh.C == 8 || sh.C == 16) && map) {
+    // one line per lane through TMA (the host passes the box map of this axis and C)
+#define ROTGP_S1(CC, RR)                                                             \
+  if (sh.C == CC && sh.R == RR)                                                      \
+    return axis == 1 ? dispatch_s1t<CC, RR, 1>(reduce, a, sh, map, s)                \
+                     : dispatch_s1t<CC, RR, 2>(reduce, a, sh, map, s);
+    ROTGP_S1(8, 3)
+    ROTGP_S1(8, 4)
+    ROTGP_S1(16, 3)
+    ROTGP_S1(16, 4)
+#undef ROTGP_S1
+    return cudaErrorInvalidValue;
+  }
   if (fp64) {
     if (sh.V == 1 && sh.C == 16) return dispatch_s<double, 1, 16>(reduce, a, sh, s);
     if (sh.V == 1 && sh.C == 64) return dispatch_s<double, 1, 64>(reduce, a, sh, s);

@@ -407,3 +407,28 @@ def test_thomas_x_launch_shapes_fp32(shape, n, h, imag):
     grid = Grid(n, h)
     ref, _ = oracle.steps(grid, Phys(**phys), oracle.init_analytic(grid, 1, R_), 20, imag)
     assert np.max(np.abs(s.get_psi() - ref)) <= 5e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("shape", [(1, 8, 3, 2), (1, 16, 4, 3), (2, 8, 3, 2), (1, 8, 4, 1)])
+@pytest.mark.parametrize("n,h", [((100, 66), (0.12, 0.15)), ((46, 36, 30), (0.3, 0.3, 0.25))])
+@pytest.mark.parametrize("imag", [True, False])
+def test_thomas_yz_launch_shapes_fp32(shape, n, h, imag):
+    """Every launch shape of the Thomas y and z sweeps (one or two lines per
+    lane, chunk, ring, segments; the last sweep also reduces the norm) gives
+    the oracle's state after 20 steps up to float rounding."""
+    V, C, R, sg = shape
+    phys = dict(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3)
+    R_ = inputs.random_phase_field(n[0], n[1], 6)
+    s = Solver(n, h, precision="fp32", **phys)
+    for ax in range(1, len(n)):
+        s.tune(ax, V, C, R, 1, sg)
+    info = s.info()
+    for ax in range(1, len(n)):
+        assert (info["lines_per_lane"][ax], info["chunk"][ax], info["ring"][ax]) == (V, C, R)
+    s.init_analytic(1, R_, 1.0, 1.0)
+    (s.step_imag if imag else s.step_real)(20)
+    grid = Grid(n, h)
+    ref, _ = oracle.steps(grid, Phys(**phys), oracle.init_analytic(grid, 1, R_), 20, imag)
+    assert np.max(np.abs(s.get_psi() - ref)) <= 5e-6 * np.max(np.abs(ref))
+    ob, refo = s.observables(), oracle.observables(grid, Phys(**phys), ref)
+    assert abs(ob["norm"] - refo["norm"]) <= 1e-5

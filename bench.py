@@ -45,6 +45,11 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default solver forms instead of timing the candidates")
+    p.add_argument("--plan", default="",
+                   help="solver form and launch shape per axis, e.g. "
+                        "thomas:1,8,4,2/thomas:1,8,3,4/thomas:2,8,3,2 (lines per lane, chunk, "
+                        "ring, segments; skips the autotuner; used to profile what a timed run "
+                        "chose, which the timed run prints as config.plan)")
     p.add_argument("--forms", default="",
                    help="solver form per axis, e.g. thomas,thomas,stencil (skips the autotuner;"
                         " used to profile the forms a timed run chose)")
@@ -224,7 +229,24 @@ def run_ours(a, w):
     R = inputs.random_phase_field(w.n[0], w.n[1], w.seed + rank)
     s.init_analytic(1, R, 1.0, 1.0)
     # solver forms picked by timing them on this grid (untimed setup, like a plan)
-    if a.forms:
+    if a.plan:
+        # form and launch shape per axis: form:V,C,R,segments separated by "/"
+        parts = a.plan.split("/")
+        if len(parts) != len(w.n):
+            raise SystemExit("--plan: one form:V,C,R,S per axis")
+        forms = []
+        for ax, part in enumerate(parts):
+            f, sh = part.split(":")
+            V, C, Rg, S = (int(v) for v in sh.split(","))
+            forms.append(f)
+            if f == "fused":
+                continue
+            s.set_solver(ax, f)
+            s.tune(ax, V, C, Rg, 1, S)
+        if "fused" in forms:
+            s.set_solver(0, "fused")
+        tuned = {"choice": -1, "forms": forms}
+    elif a.forms:
         forms = a.forms.split(",")
         if len(forms) != len(w.n) or not set(forms) <= {"thomas", "stencil", "fused"}:
             raise SystemExit("--forms: one of thomas/stencil/fused per axis")
@@ -321,6 +343,7 @@ def run_ours(a, w):
                "sample": f"{nsteps} imaginary-time split step(s) of the {w.name} grid "
                          f"({secs:.1f} s), FP64 C oracle, 1 thread"}
 
+    info = s.info()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -339,7 +362,11 @@ def run_ours(a, w):
                              "state can stay L2-resident within a step",
                        "parallelism": f"replicas x{world}",
                        "solver_forms": tuned["forms"],
-                       "solver": s.info()},
+                       "plan": "/".join(
+                           f"{f}:{info['lines_per_lane'][ax]},{info['chunk'][ax]},"
+                           f"{info['ring'][ax]},{info['segments'][ax]}"
+                           for ax, f in enumerate(tuned["forms"])),
+                       "solver": info},
             "gpu_launches": launches,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -216,9 +216,9 @@ int rotgp_set_solver(rotgp_ctx* ctx, int axis, int solver);
 /* Pick the fastest line-solver forms for this context by timing them.
  * Candidates: every combination of ROTGP_SOLVER_THOMAS / ROTGP_SOLVER_STENCIL
  * per axis that the context supports, and the fused x-y pass with each form
- * of the z sweep; then, for the chosen forms, the chunk length, ring depth
- * and segment count of each Thomas sweep and the segment count of each
- * stencil y/z sweep (as rotgp_tune).  Each candidate runs one warm-up step
+ * of the z sweep; then, for the chosen forms, the lines per lane, chunk
+ * length and segment count of each Thomas sweep together, its ring depth,
+ * and the segment count of each stencil y/z sweep (as rotgp_tune).  Each candidate runs one warm-up step
  * and then twice `steps` imaginary-time steps from a copy of the current
  * state, timed with CUDA events on the context's stream (the faster repeat
  * counts); the state, its pending renormalisation and the step counter are

@@ -45,11 +45,14 @@ __device__ __forceinline__ T abs2(cpx<T> a) { return a.x * a.x + a.y * a.y; }
 //             a0 = m_p (1 - 2 kappa), am = m_p (kappa - tau), ap = m_p (kappa + tau),
 //             al = -m_p A-
 //   backward  x_p = d'_p + be x_{p+1},  be = -c'_p.
+// m2 = 2 m_p serves the unfolded form of the same solve (psi' = 2y - psi
+// with A y = psi): d_p = m2 psi_p + al d_{p-1}, z_p = d_p + be z_{p+1},
+// psi'_p = z_p - psi_p.
 // Entry 0 is all zero (the Dirichlet edge); entries past the table length
 // equal the last one (the Toeplitz fixed point).
 template <class T>
 struct __align__(16) coef5 {
-  cpx<T> a0, am, ap, al, be;
+  cpx<T> a0, am, ap, al, be, m2;
 };
 
 // Coefficients of one sweep axis in one propagation mode.  For a line with
@@ -163,11 +166,15 @@ struct sweep_shape {
 
 cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis_coef& co,
                           cudaStream_t s);
+// map: rows TMA map of the input buffer or null; omap: the swizzled
+// one-row-per-lane map of the output buffer (that form only) or null
 cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,
-                           const void* map, cudaStream_t s);  // map: rows TMA map or null
+                           const void* map, const void* omap, cudaStream_t s);
+// map / omap: one-line-per-lane TMA box maps (C points along the line) of
+// the input and output buffers, or null
 cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
-                                 const sweep_shape& sh, const void* map, int axis,
-                                 cudaStream_t s);  // map: one-line-per-lane TMA map or null
+                                 const sweep_shape& sh, const void* map, const void* omap,
+                                 int axis, cudaStream_t s);
 // blocks of the one-line-per-lane strided form with one warp per block
 long long strided1_blocks(long long nlines, int nx, int nseg);
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);

@@ -478,7 +478,7 @@ void build_maps(rotgp_ctx* c) {
   for (int b = 0; b < 2 && c->smaps_ok; ++b)
     for (int ax = 1; ax < c->grid.dim && c->smaps_ok; ++ax)
       for (int ci = 0; ci < 2 && c->smaps_ok; ++ci) {
-        const unsigned pts = (ci == 0 ? 8 : 16) + 1;
+        const unsigned pts = ci == 0 ? 8 : 16;
         c->smaps_ok = encode_state_map(&c->map_s1[b][ax - 1][ci], c->psi[b], c->nx, c->ny,
                                        c->nz, 64, ax == 1 ? pts : 1, ax == 1 ? 1 : pts) == 0;
       }
@@ -487,7 +487,8 @@ void build_maps(rotgp_ctx* c) {
   for (int b = 0; b < 2 && c->xpass_ok; ++b)
     c->xpass_ok = encode_state_map(&c->map_xp[b], c->psi[b], c->nx, c->ny, c->nz,
                                    2 * (64 + 2 * c->axis[0].sK + 2), 32, 1) == 0;
-  // the Thomas x sweep: boxes of 64 rows x (C + 2) points
+  // the Thomas x sweep: boxes of 64 rows x (C + 2) points (two rows per
+  // lane) and swizzled boxes of 32 rows x C points (one row per lane)
   c->xmaps_ok = !c->fp64 && c->nx % 2 == 0;
   for (int b = 0; b < 2 && c->xmaps_ok; ++b)
     for (int ci = 0; ci < 2 && c->xmaps_ok; ++ci) {
@@ -495,7 +496,7 @@ void build_maps(rotgp_ctx* c) {
       c->xmaps_ok = encode_rows_map(&c->map_x[b][ci], c->psi[b], c->nx,
                                     (long long)c->ny * c->nz, 2 * (C + 2), 64) == 0 &&
                     encode_rows_map(&c->map_x1[b][ci], c->psi[b], c->nx,
-                                    (long long)c->ny * c->nz, 2 * (C + 2), 32) == 0;
+                                    (long long)c->ny * c->nz, 2 * C, 32, 8 * C) == 0;
     }
   c->maps_ok = ok;
   if (!ok) {
@@ -665,11 +666,13 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
       const long long warps = ((ap.lines + 1) / 2) * ((ap.len + 127) / 128);
       e = launch_stencil_x(imag, a, warps, c->stream);
     } else {
-      const void* xm = nullptr;
-      if (c->xmaps_ok && c->x_tma && ap.sh.vec16 && (ap.sh.C == 8 || ap.sh.C == 16))
-        xm = ap.sh.V == 2 ? &c->map_x[c->cur][ap.sh.C == 8 ? 0 : 1]
-                          : &c->map_x1[c->cur][ap.sh.C == 8 ? 0 : 1];
-      e = launch_sweep_x(c->fp64, imag, a, ap.sh, xm, c->stream);
+      const void *xm = nullptr, *om = nullptr;
+      if (c->xmaps_ok && c->x_tma && ap.sh.vec16 && (ap.sh.C == 8 || ap.sh.C == 16)) {
+        const int ci = ap.sh.C == 8 ? 0 : 1;
+        xm = ap.sh.V == 2 ? &c->map_x[c->cur][ci] : &c->map_x1[c->cur][ci];
+        om = ap.sh.V == 2 ? nullptr : &c->map_x1[1 - c->cur][ci];
+      }
+      e = launch_sweep_x(c->fp64, imag, a, ap.sh, xm, om, c->stream);
     }
   } else {
     a.stride = axis == 1 ? (long long)c->nx : (long long)c->nx * c->ny;
@@ -684,10 +687,12 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
       e = launch_line_pass(axis, last, ap.sK, axis == 1 ? &c->map_y[c->cur] : &c->map_z[c->cur],
                            ta, line_blocks(c, axis), c->stream);
     } else {
-      const void* sm = nullptr;
-      if (c->smaps_ok && ap.sh.V == 1 && (ap.sh.C == 8 || ap.sh.C == 16))
+      const void *sm = nullptr, *om = nullptr;
+      if (c->smaps_ok && ap.sh.V == 1 && (ap.sh.C == 8 || ap.sh.C == 16)) {
         sm = &c->map_s1[c->cur][axis - 1][ap.sh.C == 8 ? 0 : 1];
-      e = launch_sweep_strided(c->fp64, last, a, ap.sh, sm, axis, c->stream);
+        om = &c->map_s1[1 - c->cur][axis - 1][ap.sh.C == 8 ? 0 : 1];
+      }
+      e = launch_sweep_strided(c->fp64, last, a, ap.sh, sm, om, axis, c->stream);
     }
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
@@ -770,16 +775,20 @@ int dev_alloc(rotgp_ctx* c, void** p, size_t bytes) {
 
 namespace rotgp {
 int encode_rows_map(CUtensorMap* map, void* base, int nx, long long nrows, unsigned box0,
-                    unsigned box1) {
+                    unsigned box1, int swizzle_bytes) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
   if (!fn) return -1;
   const cuuint64_t dims[2] = {2ull * (cuuint64_t)nx, (cuuint64_t)nrows};
   const cuuint64_t strides[1] = {8ull * (cuuint64_t)nx};
   const cuuint32_t box[2] = {box0, box1};
   const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
+  if (swizzle_bytes != 0 && box0 * 4u != (unsigned)swizzle_bytes) return -1;
   return (int)fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
 int encode_state_map(CUtensorMap* map, void* base, int nx, int ny, int nz, unsigned box0,
@@ -1327,7 +1336,8 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
   for (int ax = 0; ax < dim && e == cudaSuccess && !rc; ++ax) {
     AxisPlan& ap = c->axis[ax];
     if (ap.use_stencil || (ax <= 1 && c->fuse_xy)) continue;
-    // chunk length and ring depth first (segment count kept), then segments
+    // lines per lane, chunk length and segment count together (they decide
+    // the warp count and the warm-up overhead jointly), then the ring depth
     for (int phase = 0; phase < 2 && e == cudaSuccess && !rc; ++phase) {
       const AxisPlan keep = ap;
       AxisPlan best_plan = keep;
@@ -1337,11 +1347,13 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
           const bool lean_ok = !c->fp64 && (ax == 0 ? c->xmaps_ok : c->smaps_ok);
           if (V != keep.sh.V && !lean_ok) continue;
           for (int C : {8, 16, 64})
-            for (int R : {3, 4}) shapes.push_back({V, C, R, keep.nseg});
+            for (int sg : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
+              if (sg > (ap.len + C - 1) / C) continue;
+              shapes.push_back({V, C, keep.sh.R, sg});
+            }
         }
       } else {
-        for (int sg : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
-          shapes.push_back({keep.sh.V, keep.sh.C, keep.sh.R, sg});
+        for (int R : {3, 4}) shapes.push_back({keep.sh.V, keep.sh.C, R, keep.nseg});
       }
       for (const auto& sh : shapes) {
         if (sh[0] == keep.sh.V && sh[1] == keep.sh.C && sh[2] == keep.sh.R && sh[3] == keep.nseg)

@@ -8,6 +8,8 @@
 // [point][lane] slab of the ring (no bank conflicts, no cross-lane sharing)
 // and stores its results straight to global memory, coalesced.  The solver
 // and the ring are described in sweep_common.cuh.
+#include <algorithm>
+
 #include "sweep_common.cuh"
 #include "tma.cuh"
 
@@ -41,7 +43,7 @@ __global__ void k_tables(coef5<T>* tab, int nlines, int lt, axis_coef co) {
   const dcx diag = dsub(one, {2.0 * kap.x, 2.0 * kap.y});
   const dcx kmt = dsub(kap, tau), kpt{kap.x + tau.x, kap.y + tau.y};
   coef5<T>* t = tab + (size_t)l * (lt + 1);
-  t[0].a0 = t[0].am = t[0].ap = t[0].al = t[0].be = zero<T>();
+  t[0].a0 = t[0].am = t[0].ap = t[0].al = t[0].be = t[0].m2 = zero<T>();
   dcx c{0.0, 0.0};
   for (int p = 1; p <= lt; ++p) {
     const dcx m = dinv(dsub(a0, dmul(am, c)));
@@ -52,6 +54,7 @@ __global__ void k_tables(coef5<T>* tab, int nlines, int lt, axis_coef co) {
     const dcx mam = dmul(m, am);
     t[p].al = dcast<T>({-mam.x, -mam.y});
     t[p].be = dcast<T>({-c.x, -c.y});
+    t[p].m2 = dcast<T>({2.0 * m.x, 2.0 * m.y});
   }
 }
 
@@ -353,10 +356,21 @@ cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis
   return cudaGetLastError();
 }
 
+size_t s1t_smem_per_warp(int C, int R) { return (size_t)(R + 1) * C * 32 * 8; }
+
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R) {
   const size_t e = fp64 ? 16 : 8;
-  if (x_sweep) return (size_t)R * (32 * V) * (fp64 ? C + 1 : C + 2) * e;
-  return (size_t)R * (C + 1) * 32 * V * e;
+  if (x_sweep) {
+    const size_t chunked = (size_t)R * (32 * V) * (fp64 ? C + 1 : C + 2) * e;
+    // one row per lane in complex float: the TMA form, R + 1 slots of 32 x C
+    if (!fp64 && V == 1 && (C == 8 || C == 16))
+      return std::max(chunked, (size_t)(R + 1) * 32 * C * 8);
+    return chunked;
+  }
+  const size_t chunked = (size_t)R * (C + 1) * 32 * V * e;
+  // one line per lane in complex float: the TMA form may serve it
+  if (!fp64 && V == 1 && (C == 8 || C == 16)) return std::max(chunked, s1t_smem_per_warp(C, R));
+  return chunked;
 }
 
 cudaError_t allow_smem(const void* fn, bool* done) {
@@ -399,31 +413,42 @@ static cudaError_t dispatch_s2(bool reduce, const stream_args& a, const sweep_sh
 
 // Every (precision, V, C) combination the host can choose is instantiated
 // here; anything else is rejected before a launch.
-// One line per lane, complex float, chunks by TMA (the strided counterpart
-// of k_sweep_x1t).  A warp owns 32 consecutive x of one transverse position
-// (z for y lines, AX = 1; y for z lines, AX = 2): one line position of its
-// 32 lines is 256 contiguous bytes, so each chunk of C + 1 positions is one
-// 3-D TMA box landing as [position][lane] (conflict-free 8-byte shared
-// reads), and every output position is one coalesced 256-byte store straight
-// from registers.  Arithmetic on the interleaved (re, im) layout with two
-// packed-FP32x2 accumulators, as in k_sweep_x1t.
+// One line per lane, complex float, TMA in and out.  A warp owns 32
+// consecutive x of one transverse position (z for y lines, AX = 1; y for z
+// lines, AX = 2): one line position of its 32 lines is 256 contiguous bytes,
+// so a chunk of C positions is one 3-D TMA box landing as [position][lane]
+// (conflict-free 8-byte shared reads), and the finished chunk leaves the
+// same slot as one TMA box store.
+//
+// The step is solved unfolded: with A y = psi, psi' = 2y - psi, so
+//   forward   d_p = m2_p psi_p + al_p d_{p-1}          (m2 = 2 m)
+//   backward  z_p = d_p + be_p z_{p+1},   psi'_p = z_p - psi_p
+// (two complex multiply-adds forward, one back, and no neighbour points).
+// d of a chunk stays in registers until the chunk's back substitution one
+// chunk later, which starts from a truncated carry: the next chunk back-
+// substituted from zero at its end (C >= H points, error below decay^H).
+// The ring holds R + 1 slots: R - 1 chunk loads in flight ahead of the
+// forward sweep, the chunk being back-substituted, and one more whose store
+// may still be reading shared memory.  Arithmetic on the interleaved
+// (re, im) layout with packed FP32x2 (cacc form, sweep_common.cuh).
 template <int C, bool REDUCE, int RING, int AX>
 __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUtensorMap map,
+                                                   const __grid_constant__ CUtensorMap omap,
                                                    const stream_args a) {
-  constexpr int R = RING;
-  constexpr int SLOT = (C + 1) * 32;  // float2 per slot
-  static_assert((SLOT * 8) % 128 == 0, "TMA slots");
+  constexpr int NS = RING + 1;        // slots per warp
+  constexpr int SLOT = C * 32;        // float2 per slot
+  static_assert((SLOT * 8) % 128 == 0 && NS <= 8, "TMA slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[4 * 4];
+  __shared__ __align__(8) uint64_t bars[4 * 8];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.ring != R || blockDim.x > 128 ||
-      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT * 8) + 128u) {
+  if (a.ring != RING || blockDim.x > 128 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(NS * SLOT * 8) + 128u) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
   }
   unsigned char* sbase = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
-  float2* ring = reinterpret_cast<float2*>(sbase) + (size_t)wib * R * SLOT;
-  uint64_t* bar = bars + wib * 4;
+  float2* ring = reinterpret_cast<float2*>(sbase) + (size_t)wib * NS * SLOT;
+  uint64_t* bar = bars + wib * 8;
   const int tiles_x = (a.nx + 31) / 32;
   const int nt = (int)(a.nlines / a.nx);  // transverse positions
   const long long ngroups = (long long)tiles_x * nt;
@@ -438,154 +463,183 @@ __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUten
     const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
     const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
     const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
-    const long long base = (long long)gt * a.outer + x;  // the line's point 0
-    float2* out = static_cast<float2*>(a.out) + (act ? base : 0);
     const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) +
                                (size_t)(a.coef_mode == 1 && act ? x : 0) * (lt + 1);
-    float2 A0R, A0I, AMR, AMI, APR, API, ALR, ALI, BER, BEI;
+    float2 M2R, M2I, ALR, ALI, BER, BEI;
     {
       const coef5<float> cf = crow[lt];
-      wsplit(make_float2(cf.a0.x, cf.a0.y), A0R, A0I);
-      wsplit(make_float2(cf.am.x, cf.am.y), AMR, AMI);
-      wsplit(make_float2(cf.ap.x, cf.ap.y), APR, API);
+      wsplit(make_float2(cf.m2.x, cf.m2.y), M2R, M2I);
       wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
       wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
     }
-    auto fwd_fast = [&](float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
-      float2 A = __fmul2_rn(A0R, pc), B = __fmul2_rn(A0I, pc);
-      A = __ffma2_rn(AMR, pm, A);
-      B = __ffma2_rn(AMI, pm, B);
-      A = __ffma2_rn(APR, pn, A);
-      B = __ffma2_rn(API, pn, B);
-      A = __ffma2_rn(ALR, d, A);
-      B = __ffma2_rn(ALI, d, B);
+    const float2 NEG1 = make_float2(-1.f, -1.f);
+    // d_p = m2 psi_p + al d_{p-1}
+    auto fwd = [](float2 mr, float2 mi, float2 lr, float2 li, float2 psi, float2 d) -> float2 {
+      float2 A = __fmul2_rn(mr, psi), B = __fmul2_rn(mi, psi);
+      A = __ffma2_rn(lr, d, A);
+      B = __ffma2_rn(li, d, B);
       return make_float2(A.x - B.y, A.y + B.x);
     };
-    auto fwd_tab = [&](int p, float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
-      const coef5<float> k = crow[min(p, lt)];
-      cacc c = cacc_zero();
-      float2 wr, wi;
-      wsplit(make_float2(k.a0.x, k.a0.y), wr, wi);
-      cmac(c, wr, wi, pc);
-      wsplit(make_float2(k.am.x, k.am.y), wr, wi);
-      cmac(c, wr, wi, pm);
-      wsplit(make_float2(k.ap.x, k.ap.y), wr, wi);
-      cmac(c, wr, wi, pn);
-      wsplit(make_float2(k.al.x, k.al.y), wr, wi);
-      cmac(c, wr, wi, d);
-      return cfin(c);
-    };
-    auto bstep = [&](float2 br, float2 bi, float2 xx, float2 dp) -> float2 {
-      const float2 A = __ffma2_rn(br, xx, dp), B = __fmul2_rn(bi, xx);
+    // z_p = d_p + be z_{p+1}
+    auto bstep = [](float2 br, float2 bi, float2 z, float2 dp) -> float2 {
+      const float2 A = __ffma2_rn(br, z, dp), B = __fmul2_rn(bi, z);
       return make_float2(A.x - B.y, A.y + B.x);
     };
-    auto be_at = [&](int p, float2& br, float2& bi) {
-      const coef5<float> k = crow[min(p, lt)];
-      wsplit(make_float2(k.be.x, k.be.y), br, bi);
+    auto coords = [&](int q, int& c1, int& c2) {
+      c1 = AX == 1 ? q * C : gt;
+      c2 = AX == 1 ? gt : q * C;
     };
-    auto slot = [&](int q) { return ring + (size_t)((q - qa) % R) * SLOT + lane; };
-    auto issue = [&](int q) {
-      if (q < qb && lane == 0) {
-        const int sl = (q - qa) % R;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
-        if (AX == 1)
-          tma_load_3d(ring + (size_t)sl * SLOT, &map, 64 * gx, q * C, gt, &bar[sl]);
-        else
-          tma_load_3d(ring + (size_t)sl * SLOT, &map, 64 * gx, gt, q * C, &bar[sl]);
-      }
+    auto issue = [&](int q, int sl) {  // lane 0
+      int c1, c2;
+      coords(q, c1, c2);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
+      tma_load_3d(ring + (size_t)sl * SLOT, &map, 64 * gx, c1, c2, &bar[sl]);
     };
     if (lane == 0) {
-      for (int i = 0; i < R; ++i) mbar_init(&bar[i], 1);
+      for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
       mbar_fence_init();
+      for (int q = qa; q < min(qa + RING - 1, qb); ++q) issue(q, q - qa);
     }
     __syncwarp();
-    for (int i = 0; i < R - 1; ++i) issue(qa + i);
-    float2 pm = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
-    bool good = true;
-    for (int q = qa; q <= qb && good; ++q) {
+    float2 d = make_float2(0.f, 0.f);
+    int sq = 0;        // slot of chunk q
+    unsigned ph = 0;   // phase parity of every slot's barrier
+    // forward over chunk q into cur[], back substitution and store of chunk
+    // q - 1 from prv[], then the load of chunk q + R - 1 (into chunk q - 2's slot)
+    auto step = [&](int q, float2 (&cur)[C], float2 (&prv)[C]) -> bool {
       if (q < qb) {
-        if (!__all_sync(0xffffffffu,
-                        mbar_wait(&bar[(q - qa) % R], (unsigned)(((q - qa) / R) & 1)))) {
-          for (int r = q + 1; r < min(q + R - 1, qb); ++r)
-            mbar_wait(&bar[(r - qa) % R], (unsigned)(((r - qa) / R) & 1));
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar[sq], (ph >> sq) & 1u))) {
+          int s = sq;
+          for (int r = q + 1; r < min(q + RING - 1, qb); ++r) {
+            s = s + 1 == NS ? 0 : s + 1;
+            mbar_wait(&bar[s], (ph >> s) & 1u);
+          }
           if (lane == 0) atomicOr(a.flags, 4);
-          good = false;
-          break;
+          return false;
         }
-        float2* sp = slot(q);
+        ph ^= 1u << sq;
+        const float2* sp = ring + (size_t)sq * SLOT + lane;
         const int p0 = q * C;
-        float2 w[C + 1];
-#pragma unroll
-        for (int r = 0; r <= C; ++r) w[r] = sp[r * 32];
         if (p0 >= lt && p0 + C <= N) {
 #pragma unroll
           for (int r = 0; r < C; ++r) {
-            const float2 pc = w[r];
-            d = fwd_fast(pm, pc, w[r + 1], d);
-            pm = pc;
-            sp[r * 32] = d;
+            d = fwd(M2R, M2I, ALR, ALI, sp[r * 32], d);
+            cur[r] = d;
           }
         } else {
 #pragma unroll
           for (int r = 0; r < C; ++r) {
-            const float2 pc = w[r];
-            d = fwd_tab(p0 + r, pm, pc, w[r + 1], d);
-            pm = pc;
-            sp[r * 32] = d;
+            const coef5<float>& k = crow[min(p0 + r, lt)];
+            float2 mr, mi, lr, li;
+            wsplit(make_float2(k.m2.x, k.m2.y), mr, mi);
+            wsplit(make_float2(k.al.x, k.al.y), lr, li);
+            d = fwd(mr, mi, lr, li, sp[r * 32], d);
+            cur[r] = d;
           }
         }
       }
       const int qq = q - 1;
+      bool stored = false;
       if (qq >= qo0 && qq < qo1) {
-        float2 xx = make_float2(0.f, 0.f);
-        const int la = min(a.halo, N - q * C);
-        const float2* sq = slot(q);
-        const bool la_fast = q * C >= lt;
+        float2 z = make_float2(0.f, 0.f);
+        if (q < qb) {
+          const int p0 = q * C;
+          if (p0 >= lt && p0 + C <= N) {
 #pragma unroll
-        for (int h = C - 1; h >= 0; --h) {
-          if (h >= la) continue;  // the halo is at most one chunk
-          float2 br = BER, bi = BEI;
-          if (!la_fast) be_at(q * C + h, br, bi);
-          xx = bstep(br, bi, xx, sq[h * 32]);
+            for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
+          } else {
+#pragma unroll
+            for (int h = C - 1; h >= 0; --h)
+              if (p0 + h < N) {
+                const coef5<float>& k = crow[min(p0 + h, lt)];
+                float2 br, bi;
+                wsplit(make_float2(k.be.x, k.be.y), br, bi);
+                z = bstep(br, bi, z, cur[h]);
+              }
+          }
         }
-        const float2* sp = slot(qq);
+        const int sl = sq == 0 ? NS - 1 : sq - 1;
+        float2* sp = ring + (size_t)sl * SLOT + lane;
         const int p0 = qq * C;
-        float2 w[C];
+        float2 n2 = make_float2(0.f, 0.f);
+        if (p0 >= lt && p0 + C <= N) {
 #pragma unroll
-        for (int r = 0; r < C; ++r) w[r] = sp[r * 32];
-        const bool fast = p0 >= lt && q * C <= N;
+          for (int r = C - 1; r >= 0; --r) {
+            z = bstep(BER, BEI, z, prv[r]);
+            const float2 o = __ffma2_rn(NEG1, sp[r * 32], z);
+            sp[r * 32] = o;
+            if (REDUCE) n2 = __ffma2_rn(o, o, n2);
+          }
+        } else {
 #pragma unroll
-        for (int r = C - 1; r >= 0; --r) {
-          const int p = p0 + r;
-          if (!fast && p >= N) continue;
-          float2 br = BER, bi = BEI;
-          if (!fast) be_at(p, br, bi);
-          xx = bstep(br, bi, xx, w[r]);
-          if (act) out[(long long)p * a.stride] = xx;
-          if (REDUCE) acc.add(fmaf(xx.x, xx.x, xx.y * xx.y));
+          for (int r = C - 1; r >= 0; --r)
+            if (p0 + r < N) {
+              const coef5<float>& k = crow[min(p0 + r, lt)];
+              float2 br, bi;
+              wsplit(make_float2(k.be.x, k.be.y), br, bi);
+              z = bstep(br, bi, z, prv[r]);
+              const float2 o = __ffma2_rn(NEG1, sp[r * 32], z);
+              sp[r * 32] = o;
+              if (REDUCE) n2 = __ffma2_rn(o, o, n2);
+            }
         }
+        if (REDUCE && act) acc.add(n2.x + n2.y);
+        // the chunk's results are in its slot: one box store (columns past
+        // N_x and points past N are clipped by the tensor map)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          int c1, c2;
+          coords(qq, c1, c2);
+          tma_store_3d(&omap, 64 * gx, c1, c2, ring + (size_t)sl * SLOT);
+          bulk_commit();
+        }
+        stored = true;
+      }
+      // refill the slot of chunk q - 2: every lane left it before the
+      // previous step's store; its own store is the older of at most two
+      if (lane == 0 && q + RING - 1 < qb) {
+        if (stored)
+          bulk_wait_read<1>();
+        else
+          bulk_wait_read<0>();
+        int sl = sq + NS - 2;
+        if (sl >= NS) sl -= NS;
+        issue(q + RING - 1, sl);
       }
       __syncwarp();
-      issue(q + R - 1);
+      sq = sq + 1 == NS ? 0 : sq + 1;
+      return true;
+    };
+    float2 dA[C], dB[C];
+#pragma unroll
+    for (int r = 0; r < C; ++r) dA[r] = dB[r] = make_float2(0.f, 0.f);
+    for (int q = qa; q <= qb; q += 2) {
+      if (!step(q, dA, dB)) break;
+      if (q + 1 > qb) break;
+      if (!step(q + 1, dB, dA)) break;
     }
+    if (lane == 0) bulk_wait_all();
   }
   if (REDUCE) norm_epilogue(acc.value(), a);
 }
 
 template <int C, int R, int AX>
 static cudaError_t dispatch_s1t(bool reduce, const stream_args& a, const sweep_shape& sh,
-                                const void* map, cudaStream_t s) {
+                                const void* map, const void* omap, cudaStream_t s) {
   static bool done[2] = {false, false};
   if (sh.warps_per_block > 4) return cudaErrorInvalidValue;
   const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
+  const CUtensorMap& om = *static_cast<const CUtensorMap*>(omap);
   auto fn = reduce ? k_sweep_s1t<C, true, R, AX> : k_sweep_s1t<C, false, R, AX>;
   cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
   if (e != cudaSuccess) return e;
   const long long groups = (long long)((a.nx + 31) / 32) * (a.nlines / a.nx);
   const unsigned blocks =
       (unsigned)((groups * a.nseg + sh.warps_per_block - 1) / sh.warps_per_block);
-  fn<<<blocks, 32 * sh.warps_per_block, sh.smem + 128, s>>>(m, a);
+  fn<<<blocks, 32 * sh.warps_per_block, s1t_smem_per_warp(C, R) * sh.warps_per_block + 128, s>>>(
+      m, om, a);
   return cudaGetLastError();
 }
 
@@ -594,14 +648,14 @@ long long strided1_blocks(long long nlines, int nx, int nseg) {
 }
 
 cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
-                                 const sweep_shape& sh, const void* map, int axis,
-                                 cudaStream_t s) {
-  if (!fp64 && sh.V == 1 && (sh.C == 8 || sh.C == 16) && map) {
+                                 const sweep_shape& sh, const void* map, const void* omap,
+                                 int axis, cudaStream_t s) {
+  if (!fp64 && sh.V == 1 && (sh.C == 8 || sh.C == 16) && map && omap) {
     // one line per lane through TMA (the host passes the box map of this axis and C)
 #define ROTGP_S1(CC, RR)                                                             \
   if (sh.C == CC && sh.R == RR)                                                      \
-    return axis == 1 ? dispatch_s1t<CC, RR, 1>(reduce, a, sh, map, s)                \
-                     : dispatch_s1t<CC, RR, 2>(reduce, a, sh, map, s);
+    return axis == 1 ? dispatch_s1t<CC, RR, 1>(reduce, a, sh, map, omap, s)          \
+                     : dispatch_s1t<CC, RR, 2>(reduce, a, sh, map, omap, s);
     ROTGP_S1(8, 3)
     ROTGP_S1(8, 4)
     ROTGP_S1(16, 3)

@@ -471,33 +471,38 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
   if (!TMA) cp_async_wait<0>();
 }
 
-// One row per lane, complex float, chunks by TMA.  The same folded Thomas
-// recurrences as k_sweep_x2, but each lane keeps its row in the interleaved
-// (re, im) layout in which it is stored: a complex multiply-add with
-// w = wr + i wi is accumulated as A += (wr, wr) * v and B += (wi, wi) * v
-// (packed FP32x2) and finished as (A.x - B.y, A.y + B.x), so no operand is
-// ever re-paired between rows.  32 rows per warp (twice the warps of the
-// two-rows-per-lane form for the same grid).
+// One row per lane, complex float, TMA in and out.  A warp owns 32
+// consecutive rows; a chunk of C points of them is one 2-D TMA box of 32
+// rows x 8C bytes, swizzled (64-byte rows for C = 8, 128-byte rows for
+// C = 16: 16-byte unit u of row r lands at unit u ^ s(r)), so that each lane
+// reads and writes its own row with conflict-free 16-byte accesses.  The
+// lane advances its points by H1 (with the pending scale), solves the chunk
+// in the unfolded form of k_sweep_s1t (d_p = m2 psi_p + al d_{p-1};
+// z_p = d_p + be z_{p+1}; psi'_p = z_p - psi_p, psi after H1), keeps the
+// H1-advanced points in the slot for the back substitution one chunk later,
+// overwrites them with the results, and the slot leaves as one TMA box
+// store.  Ring of R + 1 slots as in k_sweep_s1t.
 template <int C, bool IMAG, int RING>
 __global__ void __launch_bounds__(128) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
+                                                   const __grid_constant__ CUtensorMap omap,
                                                    const stream_args a) {
-  using E = cpx<float>;
-  constexpr int R = RING;
-  constexpr int PITCH = C + 2;  // 16-byte units per row: conflict-free 16-byte loads
+  constexpr int NS = RING + 1;        // slots per warp
   constexpr int ROWS = 32;
-  constexpr int SLOT = ROWS * PITCH;
-  static_assert((SLOT * 8) % 128 == 0 && C % 2 == 0, "TMA slots");
+  constexpr int U = C / 2;            // 16-byte units per row
+  constexpr int SLOT = ROWS * C;      // float2 per slot (2 or 4 KB)
+  static_assert((C == 8 || C == 16) && (SLOT * 8) % 1024 == 0 && NS <= 8, "TMA slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[4 * 4];  // [warp][slot]
+  __shared__ __align__(8) uint64_t bars[4 * 8];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.ring != R || blockDim.x > 128 ||
-      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(R * SLOT * 8) + 128u) {
+  if (a.ring != RING || blockDim.x > 128 ||
+      dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(NS * SLOT * 8) + 1024u) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
   }
-  unsigned char* sbase = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
-  float2* ring = reinterpret_cast<float2*>(sbase) + (size_t)wib * R * SLOT;
-  uint64_t* bar = bars + wib * 4;
+  // swizzled boxes repeat every 1024 bytes of shared address: align to it
+  unsigned char* sbase = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
+  float2* ring = reinterpret_cast<float2*>(sbase) + (size_t)wib * NS * SLOT;
+  uint64_t* bar = bars + wib * 8;
   const long long nrows = a.nlines;
   const long long ngroups = (nrows + ROWS - 1) / ROWS;
   const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
@@ -512,16 +517,14 @@ __global__ void __launch_bounds__(128) k_sweep_x1t(const __grid_constant__ CUten
   const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
   const int jj = act ? (int)(row % a.ny) : 0, kk = act ? (int)(row / a.ny) : 0;
   const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) + (size_t)jj * (lt + 1);
-  // the converged coefficients as duplicated pairs
-  float2 A0R, A0I, AMR, AMI, APR, API, ALR, ALI, BER, BEI;
+  float2 M2R, M2I, ALR, ALI, BER, BEI;
   {
     const coef5<float> cf = crow[lt];
-    wsplit(make_float2(cf.a0.x, cf.a0.y), A0R, A0I);
-    wsplit(make_float2(cf.am.x, cf.am.y), AMR, AMI);
-    wsplit(make_float2(cf.ap.x, cf.ap.y), APR, API);
+    wsplit(make_float2(cf.m2.x, cf.m2.y), M2R, M2I);
     wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
     wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
   }
+  const float2 NEG1 = make_float2(-1.f, -1.f);
   const float yv = (float)(a.y0 + (double)jj * a.hy), zv = (float)(a.z0 + (double)kk * a.hz);
   const float vyz = (float)a.hnu2 * yv * yv + (float)a.hlam2 * zv * zv;
   const float sc = (float)(*a.scale), hg2 = (float)a.hgam2, dt = (float)a.dt, gg = (float)a.g;
@@ -540,172 +543,175 @@ __global__ void __launch_bounds__(128) k_sweep_x1t(const __grid_constant__ CUten
       return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
     }
   };
-  // d' = a0 pc + am pm + ap pn + al d' (the d'-dependent products last)
-  auto fwd_fast = [&](float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
-    float2 A = __fmul2_rn(A0R, pc), B = __fmul2_rn(A0I, pc);
-    A = __ffma2_rn(AMR, pm, A);
-    B = __ffma2_rn(AMI, pm, B);
-    A = __ffma2_rn(APR, pn, A);
-    B = __ffma2_rn(API, pn, B);
-    A = __ffma2_rn(ALR, d, A);
-    B = __ffma2_rn(ALI, d, B);
+  auto fwd = [](float2 mr, float2 mi, float2 lr, float2 li, float2 psi, float2 d) -> float2 {
+    float2 A = __fmul2_rn(mr, psi), B = __fmul2_rn(mi, psi);
+    A = __ffma2_rn(lr, d, A);
+    B = __ffma2_rn(li, d, B);
     return make_float2(A.x - B.y, A.y + B.x);
   };
-  auto fwd_tab = [&](int p, float2 pm, float2 pc, float2 pn, float2 d) -> float2 {
-    const coef5<float> k = crow[min(p, lt)];
-    cacc c = cacc_zero();
-    float2 wr, wi;
-    wsplit(make_float2(k.a0.x, k.a0.y), wr, wi);
-    cmac(c, wr, wi, pc);
-    wsplit(make_float2(k.am.x, k.am.y), wr, wi);
-    cmac(c, wr, wi, pm);
-    wsplit(make_float2(k.ap.x, k.ap.y), wr, wi);
-    cmac(c, wr, wi, pn);
-    wsplit(make_float2(k.al.x, k.al.y), wr, wi);
-    cmac(c, wr, wi, d);
-    return cfin(c);
-  };
-  // x_p = d'_p + be x_{p+1}
-  auto bstep = [&](float2 br, float2 bi, float2 x, float2 dp) -> float2 {
-    const float2 A = __ffma2_rn(br, x, dp), B = __fmul2_rn(bi, x);
+  auto bstep = [](float2 br, float2 bi, float2 z, float2 dp) -> float2 {
+    const float2 A = __ffma2_rn(br, z, dp), B = __fmul2_rn(bi, z);
     return make_float2(A.x - B.y, A.y + B.x);
   };
-  auto be_at = [&](int p, float2& br, float2& bi) {
-    const coef5<float> k = crow[min(p, lt)];
-    wsplit(make_float2(k.be.x, k.be.y), br, bi);
+  const int swz = C == 8 ? (lane >> 1) & 3 : lane & 7;  // this row's unit swizzle
+  auto unit = [&](int sl, int u) -> float4* {
+    return reinterpret_cast<float4*>(ring + (size_t)sl * SLOT + lane * C) + (u ^ swz);
   };
-  auto slot = [&](int q) { return ring + (size_t)((q - qa) % R) * SLOT; };
-  auto issue = [&](int q) {
-    if (q < qb && lane == 0) {
-      const int sl = (q - qa) % R;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
-      tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
-    }
+  auto issue = [&](int q, int sl) {  // lane 0
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
+    tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
   };
   if (lane == 0) {
-    for (int i = 0; i < R; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
     mbar_fence_init();
+    for (int q = qa; q < min(qa + RING - 1, qb); ++q) issue(q, q - qa);
   }
   __syncwarp();
-  for (int i = 0; i < R - 1; ++i) issue(qa + i);
-  float2 pm = make_float2(0.f, 0.f), d = make_float2(0.f, 0.f);
-  float* out = static_cast<float*>(a.out);
-  for (int q = qa; q <= qb; ++q) {
+  float2 d = make_float2(0.f, 0.f);
+  int sq = 0;        // slot of chunk q
+  unsigned ph = 0;   // phase parity of every slot's barrier
+  // forward over chunk q into cur[], back substitution and store of chunk
+  // q - 1 from prv[], then the load of chunk q + R - 1 (into chunk q - 2's slot)
+  auto step = [&](int q, float2 (&cur)[C], float2 (&prv)[C]) -> bool {
+    const int sp = sq == 0 ? NS - 1 : sq - 1;
     if (q < qb) {
-      if (!__all_sync(0xffffffffu, mbar_wait(&bar[(q - qa) % R], (unsigned)(((q - qa) / R) & 1)))) {
-        for (int r = q + 1; r < min(q + R - 1, qb); ++r)
-          mbar_wait(&bar[(r - qa) % R], (unsigned)(((r - qa) / R) & 1));
+      if (!__all_sync(0xffffffffu, mbar_wait(&bar[sq], (ph >> sq) & 1u))) {
+        int s = sq;
+        for (int r = q + 1; r < min(q + RING - 1, qb); ++r) {
+          s = s + 1 == NS ? 0 : s + 1;
+          mbar_wait(&bar[s], (ph >> s) & 1u);
+        }
         if (lane == 0) atomicOr(a.flags, 4);
-        return;
+        return false;
       }
-      // forward over chunk q: stage the row's C + 1 points, advance by H1, solve
-      float2* rp = slot(q) + lane * PITCH;
+      ph ^= 1u << sq;
       const int p0 = q * C;
-      float2 w[C + 1];
+      float2 w[C];
 #pragma unroll
-      for (int i = 0; i < C / 2; ++i) {
-        const float4 t = reinterpret_cast<const float4*>(rp)[i];
-        w[2 * i] = make_float2(t.x, t.y);
-        w[2 * i + 1] = make_float2(t.z, t.w);
+      for (int u = 0; u < U; ++u) {
+        const float4 t = *unit(sq, u);
+        w[2 * u] = h1(make_float2(t.x, t.y), p0 + 2 * u);
+        w[2 * u + 1] = h1(make_float2(t.z, t.w), p0 + 2 * u + 1);
       }
-      w[C] = rp[C];
-#pragma unroll
-      for (int r = 0; r <= C; ++r) w[r] = h1(w[r], p0 + r);
       if (p0 >= lt && p0 + C <= N) {
 #pragma unroll
         for (int r = 0; r < C; ++r) {
-          const float2 pc = w[r];
-          d = fwd_fast(pm, pc, w[r + 1], d);
-          pm = pc;
-          w[r] = d;
+          d = fwd(M2R, M2I, ALR, ALI, w[r], d);
+          cur[r] = d;
         }
       } else {
 #pragma unroll
         for (int r = 0; r < C; ++r) {
-          const float2 pc = w[r];
-          d = fwd_tab(p0 + r, pm, pc, w[r + 1], d);
-          pm = pc;
-          w[r] = d;
+          const coef5<float>& k = crow[min(p0 + r, lt)];
+          float2 mr, mi, lr, li;
+          wsplit(make_float2(k.m2.x, k.m2.y), mr, mi);
+          wsplit(make_float2(k.al.x, k.al.y), lr, li);
+          d = fwd(mr, mi, lr, li, w[r], d);
+          cur[r] = d;
         }
       }
+      // keep the H1-advanced points for the back substitution
 #pragma unroll
-      for (int i = 0; i < C / 2; ++i)
-        reinterpret_cast<float4*>(rp)[i] = make_float4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x,
-                                                        w[2 * i + 1].y);
+      for (int u = 0; u < U; ++u)
+        *unit(sq, u) = make_float4(w[2 * u].x, w[2 * u].y, w[2 * u + 1].x, w[2 * u + 1].y);
     }
     const int qq = q - 1;
+    bool stored = false;
     if (qq >= qo0 && qq < qo1) {
-      // back substitution: start H points into chunk q from x = 0
-      float2 x = make_float2(0.f, 0.f);
-      const int la = min(a.halo, N - q * C);
-      const float2* sq = slot(q) + lane * PITCH;
-      const bool la_fast = q * C >= lt;
+      float2 z = make_float2(0.f, 0.f);
+      if (q < qb) {
+        const int p0 = q * C;
+        if (p0 >= lt && p0 + C <= N) {
 #pragma unroll
-      for (int h = C - 1; h >= 0; --h) {
-        if (h >= la) continue;  // the halo is at most one chunk
-        float2 br = BER, bi = BEI;
-        if (!la_fast) be_at(q * C + h, br, bi);
-        x = bstep(br, bi, x, sq[h]);
+          for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
+        } else {
+#pragma unroll
+          for (int h = C - 1; h >= 0; --h)
+            if (p0 + h < N) {
+              const coef5<float>& k = crow[min(p0 + h, lt)];
+              float2 br, bi;
+              wsplit(make_float2(k.be.x, k.be.y), br, bi);
+              z = bstep(br, bi, z, cur[h]);
+            }
+        }
       }
-      float2* sp = slot(qq) + lane * PITCH;
       const int p0 = qq * C;
-      float2 w[C];
+      if (p0 >= lt && p0 + C <= N) {
 #pragma unroll
-      for (int i = 0; i < C / 2; ++i) {
-        const float4 t = reinterpret_cast<const float4*>(sp)[i];
-        w[2 * i] = make_float2(t.x, t.y);
-        w[2 * i + 1] = make_float2(t.z, t.w);
-      }
-      if (p0 >= lt && q * C <= N) {
-#pragma unroll
-        for (int r = C - 1; r >= 0; --r) {
-          x = bstep(BER, BEI, x, w[r]);
-          w[r] = x;
+        for (int u = U - 1; u >= 0; --u) {
+          const float4 t = *unit(sp, u);
+          z = bstep(BER, BEI, z, prv[2 * u + 1]);
+          const float2 o1 = __ffma2_rn(NEG1, make_float2(t.z, t.w), z);
+          z = bstep(BER, BEI, z, prv[2 * u]);
+          const float2 o0 = __ffma2_rn(NEG1, make_float2(t.x, t.y), z);
+          *unit(sp, u) = make_float4(o0.x, o0.y, o1.x, o1.y);
         }
       } else {
 #pragma unroll
-        for (int r = C - 1; r >= 0; --r) {
-          if (p0 + r < N) {
-            float2 br, bi;
-            be_at(p0 + r, br, bi);
-            x = bstep(br, bi, x, w[r]);
+        for (int u = U - 1; u >= 0; --u) {
+          const float4 t = *unit(sp, u);
+          float2 o[2];
+#pragma unroll
+          for (int e = 1; e >= 0; --e) {
+            const int r = 2 * u + e;
+            if (p0 + r < N) {
+              const coef5<float>& k = crow[min(p0 + r, lt)];
+              float2 br, bi;
+              wsplit(make_float2(k.be.x, k.be.y), br, bi);
+              z = bstep(br, bi, z, prv[r]);
+            }
+            o[e] = __ffma2_rn(NEG1, e ? make_float2(t.z, t.w) : make_float2(t.x, t.y), z);
           }
-          w[r] = x;
+          *unit(sp, u) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
         }
       }
-#pragma unroll
-      for (int i = 0; i < C / 2; ++i)
-        reinterpret_cast<float4*>(sp)[i] = make_float4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x,
-                                                        w[2 * i + 1].y);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      // copy the chunk out: 16-byte pieces, consecutive lanes along a row
-      const float2* sbase_q = slot(qq);
-#pragma unroll
-      for (int i = 0; i < ROWS * (C / 2) / 32; ++i) {
-        const int t = i * 32 + lane, rr = t / (C / 2), cc = t % (C / 2);
-        const long long orow = row0 + rr;
-        const int p = p0 + 2 * cc;
-        if (orow < nrows && p < N)
-          *reinterpret_cast<float4*>(out + 2 * (orow * N + p)) =
-              *reinterpret_cast<const float4*>(sbase_q + rr * PITCH + 2 * cc);
+      if (lane == 0) {
+        tma_store_2d(&omap, 2 * qq * C, (int)row0, ring + (size_t)sp * SLOT);
+        bulk_commit();
       }
+      stored = true;
+    }
+    if (lane == 0 && q + RING - 1 < qb) {
+      if (stored)
+        bulk_wait_read<1>();
+      else
+        bulk_wait_read<0>();
+      int sl = sq + NS - 2;
+      if (sl >= NS) sl -= NS;
+      issue(q + RING - 1, sl);
     }
     __syncwarp();
-    issue(q + R - 1);
+    sq = sq + 1 == NS ? 0 : sq + 1;
+    return true;
+  };
+  float2 dA[C], dB[C];
+#pragma unroll
+  for (int r = 0; r < C; ++r) dA[r] = dB[r] = make_float2(0.f, 0.f);
+  for (int q = qa; q <= qb; q += 2) {
+    if (!step(q, dA, dB)) break;
+    if (q + 1 > qb) break;
+    if (!step(q + 1, dB, dA)) break;
   }
+  if (lane == 0) bulk_wait_all();
 }
+
+size_t x1t_smem_per_warp(int C, int R) { return (size_t)(R + 1) * 32 * C * 8; }
 
 template <int C, int R>
 static cudaError_t dispatch_x1t(bool imag, const stream_args& a, const sweep_shape& sh,
-                                const void* map, cudaStream_t s) {
+                                const void* map, const void* omap, cudaStream_t s) {
   static bool done[2] = {false, false};
   if (sh.warps_per_block > 4) return cudaErrorInvalidValue;
   const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
+  const CUtensorMap& om = *static_cast<const CUtensorMap*>(omap);
   auto fn = imag ? k_sweep_x1t<C, true, R> : k_sweep_x1t<C, false, R>;
   cudaError_t e = allow_smem((const void*)fn, &done[imag ? 1 : 0]);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem + 128, s>>>(m, a);
+  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block,
+       x1t_smem_per_warp(C, R) * sh.warps_per_block + 1024, s>>>(m, om, a);
   return cudaGetLastError();
 }
 
@@ -751,7 +757,7 @@ static cudaError_t dispatch_x(bool imag, bool vec16, const stream_args& a, const
 // Every (precision, V, C) combination the host can choose is instantiated
 // here; anything else is rejected before a launch.
 cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,
-                           const void* map, cudaStream_t s) {
+                           const void* map, const void* omap, cudaStream_t s) {
   if (fp64) {
     if (sh.V == 1 && sh.C == 16) return dispatch_x<double, 1, 16>(imag, true, a, sh, s);
     if (sh.V == 1 && sh.C == 64) return dispatch_x<double, 1, 64>(imag, true, a, sh, s);
@@ -759,12 +765,12 @@ cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const swe
   }
   if (sh.V == 2 && sh.C == 8) return dispatch_x2<8>(imag, sh.vec16, a, sh, map, s);
   if (sh.V == 2 && sh.C == 16) return dispatch_x2<16>(imag, sh.vec16, a, sh, map, s);
-  // one row per lane through TMA (the host passes the 32-row map)
-  if (sh.V == 1 && (sh.C == 8 || sh.C == 16) && sh.vec16 && map) {
-    if (sh.C == 8) return sh.R == 3 ? dispatch_x1t<8, 3>(imag, a, sh, map, s)
-                                    : dispatch_x1t<8, 4>(imag, a, sh, map, s);
-    return sh.R == 3 ? dispatch_x1t<16, 3>(imag, a, sh, map, s)
-                     : dispatch_x1t<16, 4>(imag, a, sh, map, s);
+  // one row per lane through TMA (the host passes the swizzled 32-row maps)
+  if (sh.V == 1 && (sh.C == 8 || sh.C == 16) && sh.vec16 && map && omap) {
+    if (sh.C == 8) return sh.R == 3 ? dispatch_x1t<8, 3>(imag, a, sh, map, omap, s)
+                                    : dispatch_x1t<8, 4>(imag, a, sh, map, omap, s);
+    return sh.R == 3 ? dispatch_x1t<16, 3>(imag, a, sh, map, omap, s)
+                     : dispatch_x1t<16, 4>(imag, a, sh, map, omap, s);
   }
   if (sh.V == 1 && sh.C == 16) return dispatch_x<float, 1, 16>(imag, sh.vec16, a, sh, s);
   if (sh.V == 1 && sh.C == 64) return dispatch_x<float, 1, 64>(imag, sh.vec16, a, sh, s);

@@ -83,11 +83,47 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 3-D tiled TMA store of the box at (c0, c1, c2) from shared memory (bulk
+// async-group of the issuing thread; elements outside the tensor are not
+// written).  The writing threads fence their shared-memory stores to the
+// async proxy and synchronise before the issuing thread calls this.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int c0, int c1, int c2,
+                                             const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(src))
+      : "memory");
+}
+// 2-D tiled TMA store of the box at (c0, c1) from shared memory.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int c0, int c1,
+                                             const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(smem_addr(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// until at most N of this thread's bulk groups still read shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// until all of this thread's bulk groups are complete
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // Host: encode a 2-D float32 tensor map over the rows of a complex-float
 // state (nrows rows of nx points; dimension 0 counts floats) with the box
 // (floats, rows).  Same return convention as encode_state_map.
+// swizzle_bytes: 0 (none), 64 or 128 (16-byte units of each box row of that
+// many bytes are permuted by the row's shared-memory address bits 7.. as the
+// tensor map's 64B / 128B swizzle modes define).
 int encode_rows_map(CUtensorMap* map, void* base, int nx, long long nrows, unsigned box0,
-                    unsigned box1);
+                    unsigned box1, int swizzle_bytes = 0);
 
 // Host: encode a 3-D float32 tensor map over a complex-float state of
 // nx x ny x nz points (x fastest; dimension 0 counts floats, 2 per point)

@@ -178,9 +178,10 @@ int rotgp_info(const rotgp_ctx* ctx, rotgp_solver_info* out);
 /* Launch shape of one sweep (axis 0 = x, 1 = y, 2 = z): lines solved per
  * GPU thread (1, or 2 for complex float), chunk length C (8, 16 or 64;
  * C >= the halo H of rotgp_info; complex float takes 8 or 16 with 2 lines
- * per thread, 16 or 64 with one; double takes 16 or 64), ring slots (3 or
- * 4), warps per block (1..8) and segments each line is split into (clamped
- * to the number of chunks).  Changes speed only: every shape gives results
+ * per thread, and 8 or 16 (TMA forms, even N_x) or 16 or 64 with one;
+ * double takes 16 or 64), ring slots (3 or 4; 5 or 6 too in the TMA forms
+ * with one line per thread and chunk 8), warps per block (1..8) and
+ * segments each line is split into (clamped to the number of chunks).  Changes speed only: every shape gives results
  * equal up to the truncation bound of the chunked line solver.  Used by the
  * autotuner.  ROTGP_EINVAL for a shape that is not built or does not fit. */
 int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring,

@@ -311,7 +311,11 @@ int set_shape(rotgp_ctx* c, int a, int V, int C, int R, int wpb, long long nseg)
   if (V == 2 && !x && c->nx % 2 != 0)
     return fail(c, ROTGP_EINVAL, "two lines per lane in y/z sweeps need an even N_x");
   if (C < c->halo) return fail(c, ROTGP_EINVAL, "chunk %d shorter than the halo %d", C, c->halo);
-  if (R != 3 && R != 4) return fail(c, ROTGP_EINVAL, "ring must have 3 or 4 slots");
+  // the one-line-per-lane TMA forms with chunk 8 also take 5 or 6 slots
+  const bool deep = !c->fp64 && V == 1 && C == 8 && c->nx % 2 == 0 &&
+                    (x ? c->xmaps_ok && c->x_tma : c->smaps_ok);
+  if (R != 3 && R != 4 && !(deep && (R == 5 || R == 6)))
+    return fail(c, ROTGP_EINVAL, "ring must have 3 or 4 slots (5 or 6 in the TMA forms, chunk 8)");
   const size_t per_warp = sweep_smem_per_warp(c->fp64, x, V, C, R);
   if (per_warp * wpb > limit) return fail(c, ROTGP_EINVAL, "launch shape exceeds shared memory");
   const int nch = (ap.len + C - 1) / C;
@@ -1353,7 +1357,7 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
             }
         }
       } else {
-        for (int R : {3, 4}) shapes.push_back({keep.sh.V, keep.sh.C, R, keep.nseg});
+        for (int R : {3, 4, 5, 6}) shapes.push_back({keep.sh.V, keep.sh.C, R, keep.nseg});
       }
       for (const auto& sh : shapes) {
         if (sh[0] == keep.sh.V && sh[1] == keep.sh.C && sh[2] == keep.sh.R && sh[3] == keep.nseg)

@@ -658,6 +658,8 @@ cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
                      : dispatch_s1t<CC, RR, 2>(reduce, a, sh, map, omap, s);
     ROTGP_S1(8, 3)
     ROTGP_S1(8, 4)
+    ROTGP_S1(8, 5)
+    ROTGP_S1(8, 6)
     ROTGP_S1(16, 3)
     ROTGP_S1(16, 4)
 #undef ROTGP_S1

@@ -767,8 +767,13 @@ cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const swe
   if (sh.V == 2 && sh.C == 16) return dispatch_x2<16>(imag, sh.vec16, a, sh, map, s);
   // one row per lane through TMA (the host passes the swizzled 32-row maps)
   if (sh.V == 1 && (sh.C == 8 || sh.C == 16) && sh.vec16 && map && omap) {
-    if (sh.C == 8) return sh.R == 3 ? dispatch_x1t<8, 3>(imag, a, sh, map, omap, s)
-                                    : dispatch_x1t<8, 4>(imag, a, sh, map, omap, s);
+    if (sh.C == 8) {
+      if (sh.R == 3) return dispatch_x1t<8, 3>(imag, a, sh, map, omap, s);
+      if (sh.R == 4) return dispatch_x1t<8, 4>(imag, a, sh, map, omap, s);
+      if (sh.R == 5) return dispatch_x1t<8, 5>(imag, a, sh, map, omap, s);
+      if (sh.R == 6) return dispatch_x1t<8, 6>(imag, a, sh, map, omap, s);
+      return cudaErrorInvalidValue;
+    }
     return sh.R == 3 ? dispatch_x1t<16, 3>(imag, a, sh, map, omap, s)
                      : dispatch_x1t<16, 4>(imag, a, sh, map, omap, s);
   }

@@ -388,7 +388,8 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
     assert abs(s.observables()["norm"] - 1.0) < 1e-5
 
 
-@pytest.mark.parametrize("shape", [(1, 8, 3, 2), (1, 16, 4, 3), (2, 8, 3, 2), (2, 16, 4, 1)])
+@pytest.mark.parametrize("shape", [(1, 8, 3, 2), (1, 16, 4, 3), (1, 8, 6, 2), (2, 8, 3, 2),
+                                   (2, 16, 4, 1)])
 @pytest.mark.parametrize("n,h", [((100, 64), (0.12, 0.15)), ((46, 36, 30), (0.3, 0.3, 0.25))])
 @pytest.mark.parametrize("imag", [True, False])
 def test_thomas_x_launch_shapes_fp32(shape, n, h, imag):
@@ -409,7 +410,8 @@ def test_thomas_x_launch_shapes_fp32(shape, n, h, imag):
     assert np.max(np.abs(s.get_psi() - ref)) <= 5e-6 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("shape", [(1, 8, 3, 2), (1, 16, 4, 3), (2, 8, 3, 2), (1, 8, 4, 1)])
+@pytest.mark.parametrize("shape", [(1, 8, 3, 2), (1, 16, 4, 3), (2, 8, 3, 2), (1, 8, 4, 1),
+                                   (1, 8, 5, 3), (1, 8, 6, 1)])
 @pytest.mark.parametrize("n,h", [((100, 66), (0.12, 0.15)), ((46, 36, 30), (0.3, 0.3, 0.25))])
 @pytest.mark.parametrize("imag", [True, False])
 def test_thomas_yz_launch_shapes_fp32(shape, n, h, imag):

@@ -178,6 +178,37 @@ cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
 // blocks of the one-line-per-lane strided form with one warp per block
 long long strided1_blocks(long long nlines, int nx, int nseg);
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);
+// Launch with programmatic stream serialization: the kernel's blocks may be
+// scheduled while the previous kernel in the stream finishes; the kernel
+// itself waits (griddep_wait) for the previous kernel's writes before it
+// touches global memory.
+template <class... P, class... A>
+cudaError_t launch_programmatic(void (*fn)(P...), unsigned blocks, unsigned threads, size_t smem,
+                                cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, static_cast<A&&>(args)...);
+}
+#ifdef __CUDACC__
+// the kernel side: allow the next kernel's blocks to launch; wait for the
+// previous kernel's completion and memory (a no-op without a dependency)
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
+// persistent grid of a warp-per-unit kernel (sweep_s.cu)
+cudaError_t resident_grid(const void* fn, long long units, size_t smem_per_warp, size_t extra,
+                          int max_warps, int* warps, unsigned* blocks);
 // banded-inverse stencil form of the complex-float sweeps (stencil.cu)
 cudaError_t launch_stencil_tables(void* wtab, int nlines, int K, int B, int m,
                                   const axis_coef& co, cudaStream_t s);

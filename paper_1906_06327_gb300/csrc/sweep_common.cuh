@@ -286,6 +286,27 @@ __device__ __forceinline__ void cmac(cacc& c, const float2& wr, const float2& wi
 __device__ __forceinline__ float2 cfin(const cacc& c) {
   return make_float2(c.a.x - c.b.y, c.a.y + c.b.x);
 }
+// Table coefficients of positions p0 .. p0 + C - 1 of one line (entries past
+// the table length are the converged ones), all loads issued together ahead
+// of the recurrence that uses them, which would otherwise wait on each load
+// in turn (the table path of the line start and of a ragged line end).
+template <int C>
+__device__ __forceinline__ void table_fwd(const coef5<float>* crow, int p0, int lt,
+                                          float2 (&m2)[C], float2 (&al)[C]) {
+#pragma unroll
+  for (int r = 0; r < C; ++r) {
+    const coef5<float>* k = crow + min(p0 + r, lt);
+    m2[r] = __ldg(reinterpret_cast<const float2*>(&k->m2));
+    al[r] = __ldg(reinterpret_cast<const float2*>(&k->al));
+  }
+}
+template <int C>
+__device__ __forceinline__ void table_be(const coef5<float>* crow, int p0, int lt,
+                                         float2 (&be)[C]) {
+#pragma unroll
+  for (int r = 0; r < C; ++r) be[r] = __ldg(reinterpret_cast<const float2*>(&crow[min(p0 + r, lt)].be));
+}
+
 // a complex weight as the two duplicated pairs (wr, wr), (wi, wi)
 __device__ __forceinline__ void wsplit(const float2& w, float2& wr, float2& wi) {
   wr = make_float2(w.x, w.x);

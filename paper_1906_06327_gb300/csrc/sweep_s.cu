@@ -9,6 +9,9 @@
 // and stores its results straight to global memory, coalesced.  The solver
 // and the ring are described in sweep_common.cuh.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "sweep_common.cuh"
 #include "tma.cuh"
@@ -373,6 +376,48 @@ size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R) {
   return chunked;
 }
 
+// Grid of a kernel whose warps take work units round-robin: W warps per
+// block (at most max_warps, and no more than the units per SM, so that the units
+// spread over every SM) and as many blocks as are resident at once, at most
+// one per W units.  One launch wave of long-lived warps replaces a block per
+// unit (block launches and, in the last sweep, norm partials per block).
+cudaError_t resident_grid(const void* fn, long long units, size_t smem_per_warp, size_t extra,
+                          int max_warps, int* warps, unsigned* blocks) {
+  int dev = 0, sms = 0, nb = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  // launch shapes are asked for every sweep launch: remember them
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, long long, size_t, size_t, int, int>,
+                  std::pair<int, unsigned>>
+      memo;
+  const auto key = std::make_tuple(fn, units, smem_per_warp, extra, max_warps, dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = memo.find(key);
+    if (it != memo.end()) {
+      *warps = it->second.first;
+      *blocks = it->second.second;
+      return cudaSuccess;
+    }
+  }
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int W = (int)std::min<long long>(max_warps, std::max<long long>(1, (units + sms - 1) / sms));
+  for (; W >= 1; --W) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * W, smem_per_warp * W + extra);
+    if (e != cudaSuccess) return e;
+    if (nb >= 1) break;
+  }
+  if (W < 1) return cudaErrorInvalidConfiguration;
+  *warps = W;
+  *blocks = (unsigned)std::max<long long>(
+      1, std::min<long long>((units + W - 1) / W, (long long)sms * nb));
+  std::lock_guard<std::mutex> lk(mu);
+  memo[key] = {*warps, *blocks};
+  return cudaSuccess;
+}
+
 cudaError_t allow_smem(const void* fn, bool* done) {
   if (*done) return cudaSuccess;
   int dev = 0, optin = 0;
@@ -432,16 +477,16 @@ static cudaError_t dispatch_s2(bool reduce, const stream_args& a, const sweep_sh
 // may still be reading shared memory.  Arithmetic on the interleaved
 // (re, im) layout with packed FP32x2 (cacc form, sweep_common.cuh).
 template <int C, bool REDUCE, int RING, int AX>
-__global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_constant__ CUtensorMap map,
                                                    const __grid_constant__ CUtensorMap omap,
                                                    const stream_args a) {
   constexpr int NS = RING + 1;        // slots per warp
   constexpr int SLOT = C * 32;        // float2 per slot
   static_assert((SLOT * 8) % 128 == 0 && NS <= 8, "TMA slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[4 * 8];
+  __shared__ __align__(8) uint64_t bars[16 * 8];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.ring != RING || blockDim.x > 128 ||
+  if (a.ring != RING || blockDim.x > (C == 8 ? 512u : 256u) ||
       dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(NS * SLOT * 8) + 128u) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
@@ -452,9 +497,25 @@ __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUten
   const int tiles_x = (a.nx + 31) / 32;
   const int nt = (int)(a.nlines / a.nx);  // transverse positions
   const long long ngroups = (long long)tiles_x * nt;
-  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
   acc_t<float> acc;
-  if (wg < ngroups * a.nseg) {
+  if (lane == 0) {
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  // launched programmatically: the next sweep's blocks may be scheduled as
+  // SMs free up; the previous kernel's state and pending scale are complete
+  // and visible past this wait, and nothing above touched global memory
+  griddep_launch_dependents();
+  griddep_wait();
+  unsigned ph = 0;  // phase parity of every slot's barrier, kept from unit to unit
+  bool good = true;
+  // units (a patch of 32 lines and one segment of them) in a fixed
+  // round-robin order over the resident warps
+  const long long nunits = ngroups * a.nseg;
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib; wg < nunits && good;
+       wg += wstride) {
     const long long g = wg % ngroups;
     const int sg = (int)(wg / ngroups);
     const int gx = (int)(g % tiles_x), gt = (int)(g / tiles_x);
@@ -497,14 +558,12 @@ __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUten
       tma_load_3d(ring + (size_t)sl * SLOT, &map, 64 * gx, c1, c2, &bar[sl]);
     };
     if (lane == 0) {
-      for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
-      mbar_fence_init();
+      bulk_wait_read<0>();  // the previous unit's stores have left their slots
       for (int q = qa; q < min(qa + RING - 1, qb); ++q) issue(q, q - qa);
     }
     __syncwarp();
     float2 d = make_float2(0.f, 0.f);
-    int sq = 0;        // slot of chunk q
-    unsigned ph = 0;   // phase parity of every slot's barrier
+    int sq = 0;  // slot of chunk q
     // forward over chunk q into cur[], back substitution and store of chunk
     // q - 1 from prv[], then the load of chunk q + R - 1 (into chunk q - 2's slot)
     auto step = [&](int q, float2 (&cur)[C], float2 (&prv)[C]) -> bool {
@@ -528,12 +587,13 @@ __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUten
             cur[r] = d;
           }
         } else {
+float2 km[C], kl[C];
+          table_fwd<C>(crow, p0, lt, km, kl);
 #pragma unroll
           for (int r = 0; r < C; ++r) {
-            const coef5<float>& k = crow[min(p0 + r, lt)];
             float2 mr, mi, lr, li;
-            wsplit(make_float2(k.m2.x, k.m2.y), mr, mi);
-            wsplit(make_float2(k.al.x, k.al.y), lr, li);
+            wsplit(km[r], mr, mi);
+            wsplit(kl[r], lr, li);
             d = fwd(mr, mi, lr, li, sp[r * 32], d);
             cur[r] = d;
           }
@@ -549,12 +609,13 @@ __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUten
 #pragma unroll
             for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
           } else {
+            float2 kb[C];
+            table_be<C>(crow, p0, lt, kb);
 #pragma unroll
             for (int h = C - 1; h >= 0; --h)
               if (p0 + h < N) {
-                const coef5<float>& k = crow[min(p0 + h, lt)];
                 float2 br, bi;
-                wsplit(make_float2(k.be.x, k.be.y), br, bi);
+                wsplit(kb[h], br, bi);
                 z = bstep(br, bi, z, cur[h]);
               }
           }
@@ -572,12 +633,13 @@ __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUten
             if (REDUCE) n2 = __ffma2_rn(o, o, n2);
           }
         } else {
+          float2 kb[C];
+          table_be<C>(crow, p0, lt, kb);
 #pragma unroll
           for (int r = C - 1; r >= 0; --r)
             if (p0 + r < N) {
-              const coef5<float>& k = crow[min(p0 + r, lt)];
               float2 br, bi;
-              wsplit(make_float2(k.be.x, k.be.y), br, bi);
+              wsplit(kb[r], br, bi);
               z = bstep(br, bi, z, prv[r]);
               const float2 o = __ffma2_rn(NEG1, sp[r * 32], z);
               sp[r * 32] = o;
@@ -616,12 +678,18 @@ __global__ void __launch_bounds__(128) k_sweep_s1t(const __grid_constant__ CUten
 #pragma unroll
     for (int r = 0; r < C; ++r) dA[r] = dB[r] = make_float2(0.f, 0.f);
     for (int q = qa; q <= qb; q += 2) {
-      if (!step(q, dA, dB)) break;
+      if (!step(q, dA, dB)) {
+        good = false;
+        break;
+      }
       if (q + 1 > qb) break;
-      if (!step(q + 1, dB, dA)) break;
+      if (!step(q + 1, dB, dA)) {
+        good = false;
+        break;
+      }
     }
-    if (lane == 0) bulk_wait_all();
   }
+  if (lane == 0) bulk_wait_all();
   if (REDUCE) norm_epilogue(acc.value(), a);
 }
 
@@ -629,18 +697,18 @@ template <int C, int R, int AX>
 static cudaError_t dispatch_s1t(bool reduce, const stream_args& a, const sweep_shape& sh,
                                 const void* map, const void* omap, cudaStream_t s) {
   static bool done[2] = {false, false};
-  if (sh.warps_per_block > 4) return cudaErrorInvalidValue;
   const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
   const CUtensorMap& om = *static_cast<const CUtensorMap*>(omap);
   auto fn = reduce ? k_sweep_s1t<C, true, R, AX> : k_sweep_s1t<C, false, R, AX>;
   cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
   if (e != cudaSuccess) return e;
-  const long long groups = (long long)((a.nx + 31) / 32) * (a.nlines / a.nx);
-  const unsigned blocks =
-      (unsigned)((groups * a.nseg + sh.warps_per_block - 1) / sh.warps_per_block);
-  fn<<<blocks, 32 * sh.warps_per_block, s1t_smem_per_warp(C, R) * sh.warps_per_block + 128, s>>>(
-      m, om, a);
-  return cudaGetLastError();
+  const long long units = (long long)((a.nx + 31) / 32) * (a.nlines / a.nx) * a.nseg;
+  int W = 1;
+  unsigned blocks = 0;
+  e = resident_grid((const void*)fn, units, s1t_smem_per_warp(C, R), 128, C == 8 ? 16 : 8, &W,
+                    &blocks);
+  if (e != cudaSuccess) return e;
+  return launch_programmatic(fn, blocks, 32 * W, s1t_smem_per_warp(C, R) * W + 128, s, m, om, a);
 }
 
 long long strided1_blocks(long long nlines, int nx, int nseg) {

@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
 // overwrites them with the results, and the slot leaves as one TMA box
 // store.  Ring of R + 1 slots as in k_sweep_s1t.
 template <int C, bool IMAG, int RING>
-__global__ void __launch_bounds__(128) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
                                                    const __grid_constant__ CUtensorMap omap,
                                                    const stream_args a) {
   constexpr int NS = RING + 1;        // slots per warp
@@ -492,9 +492,9 @@ __global__ void __launch_bounds__(128) k_sweep_x1t(const __grid_constant__ CUten
   constexpr int SLOT = ROWS * C;      // float2 per slot (2 or 4 KB)
   static_assert((C == 8 || C == 16) && (SLOT * 8) % 1024 == 0 && NS <= 8, "TMA slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bars[4 * 8];
+  __shared__ __align__(8) uint64_t bars[16 * 8];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.ring != RING || blockDim.x > 128 ||
+  if (a.ring != RING || blockDim.x > (C == 8 ? 512u : 256u) ||
       dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(NS * SLOT * 8) + 1024u) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
@@ -505,195 +505,219 @@ __global__ void __launch_bounds__(128) k_sweep_x1t(const __grid_constant__ CUten
   uint64_t* bar = bars + wib * 8;
   const long long nrows = a.nlines;
   const long long ngroups = (nrows + ROWS - 1) / ROWS;
-  const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
-  if (wg >= ngroups * a.nseg) return;  // whole warp; no block barrier below
-  const long long g = wg % ngroups;
-  const int sg = (int)(wg / ngroups);
-  const long long row0 = g * ROWS;
-  const long long row = row0 + lane;
-  const bool act = row < nrows;
-  const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
-  const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
-  const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
-  const int jj = act ? (int)(row % a.ny) : 0, kk = act ? (int)(row / a.ny) : 0;
-  const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) + (size_t)jj * (lt + 1);
-  float2 M2R, M2I, ALR, ALI, BER, BEI;
-  {
-    const coef5<float> cf = crow[lt];
-    wsplit(make_float2(cf.m2.x, cf.m2.y), M2R, M2I);
-    wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
-    wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
-  }
-  const float2 NEG1 = make_float2(-1.f, -1.f);
-  const float yv = (float)(a.y0 + (double)jj * a.hy), zv = (float)(a.z0 + (double)kk * a.hz);
-  const float vyz = (float)a.hnu2 * yv * yv + (float)a.hlam2 * zv * zv;
-  const float sc = (float)(*a.scale), hg2 = (float)a.hgam2, dt = (float)a.dt, gg = (float)a.g;
-  const float xs = (float)a.x0, hx = (float)a.hx;
-  const float2 SC = make_float2(sc, sc);
-  auto h1 = [&](float2 v, int p) -> float2 {
-    v = __fmul2_rn(SC, v);
-    const float x = fmaf((float)p, hx, xs);
-    const float en = fmaf(gg, fmaf(v.x, v.x, v.y * v.y), fmaf(hg2 * x, x, vyz));
-    if (IMAG) {
-      const float f = __expf(-dt * en);
-      return __fmul2_rn(make_float2(f, f), v);
-    } else {
-      float sn, cs;
-      sincosf(dt * en, &sn, &cs);
-      return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
-    }
-  };
-  auto fwd = [](float2 mr, float2 mi, float2 lr, float2 li, float2 psi, float2 d) -> float2 {
-    float2 A = __fmul2_rn(mr, psi), B = __fmul2_rn(mi, psi);
-    A = __ffma2_rn(lr, d, A);
-    B = __ffma2_rn(li, d, B);
-    return make_float2(A.x - B.y, A.y + B.x);
-  };
-  auto bstep = [](float2 br, float2 bi, float2 z, float2 dp) -> float2 {
-    const float2 A = __ffma2_rn(br, z, dp), B = __fmul2_rn(bi, z);
-    return make_float2(A.x - B.y, A.y + B.x);
-  };
-  const int swz = C == 8 ? (lane >> 1) & 3 : lane & 7;  // this row's unit swizzle
-  auto unit = [&](int sl, int u) -> float4* {
-    return reinterpret_cast<float4*>(ring + (size_t)sl * SLOT + lane * C) + (u ^ swz);
-  };
-  auto issue = [&](int q, int sl) {  // lane 0
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
-    tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
-  };
   if (lane == 0) {
     for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
     mbar_fence_init();
-    for (int q = qa; q < min(qa + RING - 1, qb); ++q) issue(q, q - qa);
   }
   __syncwarp();
-  float2 d = make_float2(0.f, 0.f);
-  int sq = 0;        // slot of chunk q
-  unsigned ph = 0;   // phase parity of every slot's barrier
-  // forward over chunk q into cur[], back substitution and store of chunk
-  // q - 1 from prv[], then the load of chunk q + R - 1 (into chunk q - 2's slot)
-  auto step = [&](int q, float2 (&cur)[C], float2 (&prv)[C]) -> bool {
-    const int sp = sq == 0 ? NS - 1 : sq - 1;
-    if (q < qb) {
-      if (!__all_sync(0xffffffffu, mbar_wait(&bar[sq], (ph >> sq) & 1u))) {
-        int s = sq;
-        for (int r = q + 1; r < min(q + RING - 1, qb); ++r) {
-          s = s + 1 == NS ? 0 : s + 1;
-          mbar_wait(&bar[s], (ph >> s) & 1u);
-        }
-        if (lane == 0) atomicOr(a.flags, 4);
-        return false;
-      }
-      ph ^= 1u << sq;
-      const int p0 = q * C;
-      float2 w[C];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const float4 t = *unit(sq, u);
-        w[2 * u] = h1(make_float2(t.x, t.y), p0 + 2 * u);
-        w[2 * u + 1] = h1(make_float2(t.z, t.w), p0 + 2 * u + 1);
-      }
-      if (p0 >= lt && p0 + C <= N) {
-#pragma unroll
-        for (int r = 0; r < C; ++r) {
-          d = fwd(M2R, M2I, ALR, ALI, w[r], d);
-          cur[r] = d;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < C; ++r) {
-          const coef5<float>& k = crow[min(p0 + r, lt)];
-          float2 mr, mi, lr, li;
-          wsplit(make_float2(k.m2.x, k.m2.y), mr, mi);
-          wsplit(make_float2(k.al.x, k.al.y), lr, li);
-          d = fwd(mr, mi, lr, li, w[r], d);
-          cur[r] = d;
-        }
-      }
-      // keep the H1-advanced points for the back substitution
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        *unit(sq, u) = make_float4(w[2 * u].x, w[2 * u].y, w[2 * u + 1].x, w[2 * u + 1].y);
+  // launched programmatically: the next sweep's blocks may be scheduled as
+  // SMs free up; the previous kernel's state and pending scale are complete
+  // and visible past this wait, and nothing above touched global memory
+  griddep_launch_dependents();
+  griddep_wait();
+  unsigned ph = 0;  // phase parity of every slot's barrier, kept from unit to unit
+  bool good = true;
+  // units (32 rows and one segment of them) in a fixed round-robin order
+  // over the resident warps
+  const long long nunits = ngroups * a.nseg;
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + wib; wg < nunits && good;
+       wg += wstride) {
+    const long long g = wg % ngroups;
+    const int sg = (int)(wg / ngroups);
+    const long long row0 = g * ROWS;
+    const long long row = row0 + lane;
+    const bool act = row < nrows;
+    const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
+    const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
+    const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
+    const int jj = act ? (int)(row % a.ny) : 0, kk = act ? (int)(row / a.ny) : 0;
+    const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) + (size_t)jj * (lt + 1);
+    float2 M2R, M2I, ALR, ALI, BER, BEI;
+    {
+      const coef5<float> cf = crow[lt];
+      wsplit(make_float2(cf.m2.x, cf.m2.y), M2R, M2I);
+      wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
+      wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
     }
-    const int qq = q - 1;
-    bool stored = false;
-    if (qq >= qo0 && qq < qo1) {
-      float2 z = make_float2(0.f, 0.f);
-      if (q < qb) {
-        const int p0 = q * C;
-        if (p0 >= lt && p0 + C <= N) {
-#pragma unroll
-          for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
-        } else {
-#pragma unroll
-          for (int h = C - 1; h >= 0; --h)
-            if (p0 + h < N) {
-              const coef5<float>& k = crow[min(p0 + h, lt)];
-              float2 br, bi;
-              wsplit(make_float2(k.be.x, k.be.y), br, bi);
-              z = bstep(br, bi, z, cur[h]);
-            }
-        }
-      }
-      const int p0 = qq * C;
-      if (p0 >= lt && p0 + C <= N) {
-#pragma unroll
-        for (int u = U - 1; u >= 0; --u) {
-          const float4 t = *unit(sp, u);
-          z = bstep(BER, BEI, z, prv[2 * u + 1]);
-          const float2 o1 = __ffma2_rn(NEG1, make_float2(t.z, t.w), z);
-          z = bstep(BER, BEI, z, prv[2 * u]);
-          const float2 o0 = __ffma2_rn(NEG1, make_float2(t.x, t.y), z);
-          *unit(sp, u) = make_float4(o0.x, o0.y, o1.x, o1.y);
-        }
+    const float2 NEG1 = make_float2(-1.f, -1.f);
+    const float yv = (float)(a.y0 + (double)jj * a.hy), zv = (float)(a.z0 + (double)kk * a.hz);
+    const float vyz = (float)a.hnu2 * yv * yv + (float)a.hlam2 * zv * zv;
+    const float sc = (float)(*a.scale), hg2 = (float)a.hgam2, dt = (float)a.dt, gg = (float)a.g;
+    const float xs = (float)a.x0, hx = (float)a.hx;
+    const float2 SC = make_float2(sc, sc);
+    auto h1 = [&](float2 v, int p) -> float2 {
+      v = __fmul2_rn(SC, v);
+      const float x = fmaf((float)p, hx, xs);
+      const float en = fmaf(gg, fmaf(v.x, v.x, v.y * v.y), fmaf(hg2 * x, x, vyz));
+      if (IMAG) {
+        const float f = __expf(-dt * en);
+        return __fmul2_rn(make_float2(f, f), v);
       } else {
-#pragma unroll
-        for (int u = U - 1; u >= 0; --u) {
-          const float4 t = *unit(sp, u);
-          float2 o[2];
-#pragma unroll
-          for (int e = 1; e >= 0; --e) {
-            const int r = 2 * u + e;
-            if (p0 + r < N) {
-              const coef5<float>& k = crow[min(p0 + r, lt)];
-              float2 br, bi;
-              wsplit(make_float2(k.be.x, k.be.y), br, bi);
-              z = bstep(br, bi, z, prv[r]);
-            }
-            o[e] = __ffma2_rn(NEG1, e ? make_float2(t.z, t.w) : make_float2(t.x, t.y), z);
-          }
-          *unit(sp, u) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-        }
+        float sn, cs;
+        sincosf(dt * en, &sn, &cs);
+        return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
       }
+    };
+    auto fwd = [](float2 mr, float2 mi, float2 lr, float2 li, float2 psi, float2 d) -> float2 {
+      float2 A = __fmul2_rn(mr, psi), B = __fmul2_rn(mi, psi);
+      A = __ffma2_rn(lr, d, A);
+      B = __ffma2_rn(li, d, B);
+      return make_float2(A.x - B.y, A.y + B.x);
+    };
+    auto bstep = [](float2 br, float2 bi, float2 z, float2 dp) -> float2 {
+      const float2 A = __ffma2_rn(br, z, dp), B = __fmul2_rn(bi, z);
+      return make_float2(A.x - B.y, A.y + B.x);
+    };
+    const int swz = C == 8 ? (lane >> 1) & 3 : lane & 7;  // this row's unit swizzle
+    auto unit = [&](int sl, int u) -> float4* {
+      return reinterpret_cast<float4*>(ring + (size_t)sl * SLOT + lane * C) + (u ^ swz);
+    };
+    auto issue = [&](int q, int sl) {  // lane 0
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        tma_store_2d(&omap, 2 * qq * C, (int)row0, ring + (size_t)sp * SLOT);
-        bulk_commit();
-      }
-      stored = true;
-    }
-    if (lane == 0 && q + RING - 1 < qb) {
-      if (stored)
-        bulk_wait_read<1>();
-      else
-        bulk_wait_read<0>();
-      int sl = sq + NS - 2;
-      if (sl >= NS) sl -= NS;
-      issue(q + RING - 1, sl);
+      mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
+      tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
+    };
+    if (lane == 0) {
+      bulk_wait_read<0>();  // the previous unit's stores have left their slots
+      for (int q = qa; q < min(qa + RING - 1, qb); ++q) issue(q, q - qa);
     }
     __syncwarp();
-    sq = sq + 1 == NS ? 0 : sq + 1;
-    return true;
-  };
-  float2 dA[C], dB[C];
+    float2 d = make_float2(0.f, 0.f);
+    int sq = 0;  // slot of chunk q
+    // forward over chunk q into cur[], back substitution and store of chunk
+    // q - 1 from prv[], then the load of chunk q + R - 1 (into chunk q - 2's slot)
+    auto step = [&](int q, float2 (&cur)[C], float2 (&prv)[C]) -> bool {
+      const int sp = sq == 0 ? NS - 1 : sq - 1;
+      if (q < qb) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar[sq], (ph >> sq) & 1u))) {
+          int s = sq;
+          for (int r = q + 1; r < min(q + RING - 1, qb); ++r) {
+            s = s + 1 == NS ? 0 : s + 1;
+            mbar_wait(&bar[s], (ph >> s) & 1u);
+          }
+          if (lane == 0) atomicOr(a.flags, 4);
+          return false;
+        }
+        ph ^= 1u << sq;
+        const int p0 = q * C;
+        float2 w[C];
 #pragma unroll
-  for (int r = 0; r < C; ++r) dA[r] = dB[r] = make_float2(0.f, 0.f);
-  for (int q = qa; q <= qb; q += 2) {
-    if (!step(q, dA, dB)) break;
-    if (q + 1 > qb) break;
-    if (!step(q + 1, dB, dA)) break;
+        for (int u = 0; u < U; ++u) {
+          const float4 t = *unit(sq, u);
+          w[2 * u] = h1(make_float2(t.x, t.y), p0 + 2 * u);
+          w[2 * u + 1] = h1(make_float2(t.z, t.w), p0 + 2 * u + 1);
+        }
+        if (p0 >= lt && p0 + C <= N) {
+#pragma unroll
+          for (int r = 0; r < C; ++r) {
+            d = fwd(M2R, M2I, ALR, ALI, w[r], d);
+            cur[r] = d;
+          }
+        } else {
+  float2 km[C], kl[C];
+          table_fwd<C>(crow, p0, lt, km, kl);
+#pragma unroll
+          for (int r = 0; r < C; ++r) {
+            float2 mr, mi, lr, li;
+            wsplit(km[r], mr, mi);
+            wsplit(kl[r], lr, li);
+            d = fwd(mr, mi, lr, li, w[r], d);
+            cur[r] = d;
+          }
+        }
+        // keep the H1-advanced points for the back substitution
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          *unit(sq, u) = make_float4(w[2 * u].x, w[2 * u].y, w[2 * u + 1].x, w[2 * u + 1].y);
+      }
+      const int qq = q - 1;
+      bool stored = false;
+      if (qq >= qo0 && qq < qo1) {
+        float2 z = make_float2(0.f, 0.f);
+        if (q < qb) {
+          const int p0 = q * C;
+          if (p0 >= lt && p0 + C <= N) {
+#pragma unroll
+            for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
+          } else {
+            float2 kb[C];
+            table_be<C>(crow, p0, lt, kb);
+#pragma unroll
+            for (int h = C - 1; h >= 0; --h)
+              if (p0 + h < N) {
+                float2 br, bi;
+                wsplit(kb[h], br, bi);
+                z = bstep(br, bi, z, cur[h]);
+              }
+          }
+        }
+        const int p0 = qq * C;
+        if (p0 >= lt && p0 + C <= N) {
+#pragma unroll
+          for (int u = U - 1; u >= 0; --u) {
+            const float4 t = *unit(sp, u);
+            z = bstep(BER, BEI, z, prv[2 * u + 1]);
+            const float2 o1 = __ffma2_rn(NEG1, make_float2(t.z, t.w), z);
+            z = bstep(BER, BEI, z, prv[2 * u]);
+            const float2 o0 = __ffma2_rn(NEG1, make_float2(t.x, t.y), z);
+            *unit(sp, u) = make_float4(o0.x, o0.y, o1.x, o1.y);
+          }
+        } else {
+          float2 kb[C];
+          table_be<C>(crow, p0, lt, kb);
+#pragma unroll
+          for (int u = U - 1; u >= 0; --u) {
+            const float4 t = *unit(sp, u);
+            float2 o[2];
+#pragma unroll
+            for (int e = 1; e >= 0; --e) {
+              const int r = 2 * u + e;
+              if (p0 + r < N) {
+                float2 br, bi;
+                wsplit(kb[r], br, bi);
+                z = bstep(br, bi, z, prv[r]);
+              }
+              o[e] = __ffma2_rn(NEG1, e ? make_float2(t.z, t.w) : make_float2(t.x, t.y), z);
+            }
+            *unit(sp, u) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&omap, 2 * qq * C, (int)row0, ring + (size_t)sp * SLOT);
+          bulk_commit();
+        }
+        stored = true;
+      }
+      if (lane == 0 && q + RING - 1 < qb) {
+        if (stored)
+          bulk_wait_read<1>();
+        else
+          bulk_wait_read<0>();
+        int sl = sq + NS - 2;
+        if (sl >= NS) sl -= NS;
+        issue(q + RING - 1, sl);
+      }
+      __syncwarp();
+      sq = sq + 1 == NS ? 0 : sq + 1;
+      return true;
+    };
+    float2 dA[C], dB[C];
+#pragma unroll
+    for (int r = 0; r < C; ++r) dA[r] = dB[r] = make_float2(0.f, 0.f);
+    for (int q = qa; q <= qb; q += 2) {
+      if (!step(q, dA, dB)) {
+        good = false;
+        break;
+      }
+      if (q + 1 > qb) break;
+      if (!step(q + 1, dB, dA)) {
+        good = false;
+        break;
+      }
+    }
   }
   if (lane == 0) bulk_wait_all();
 }
@@ -704,15 +728,18 @@ template <int C, int R>
 static cudaError_t dispatch_x1t(bool imag, const stream_args& a, const sweep_shape& sh,
                                 const void* map, const void* omap, cudaStream_t s) {
   static bool done[2] = {false, false};
-  if (sh.warps_per_block > 4) return cudaErrorInvalidValue;
   const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
   const CUtensorMap& om = *static_cast<const CUtensorMap*>(omap);
   auto fn = imag ? k_sweep_x1t<C, true, R> : k_sweep_x1t<C, false, R>;
   cudaError_t e = allow_smem((const void*)fn, &done[imag ? 1 : 0]);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block,
-       x1t_smem_per_warp(C, R) * sh.warps_per_block + 1024, s>>>(m, om, a);
-  return cudaGetLastError();
+  const long long units = (a.nlines + 31) / 32 * a.nseg;
+  int W = 1;
+  unsigned blocks = 0;
+  e = resident_grid((const void*)fn, units, x1t_smem_per_warp(C, R), 1024, C == 8 ? 16 : 8, &W,
+                    &blocks);
+  if (e != cudaSuccess) return e;
+  return launch_programmatic(fn, blocks, 32 * W, x1t_smem_per_warp(C, R) * W + 1024, s, m, om, a);
 }
 
 template <int C, int R>

@@ -7,7 +7,7 @@
 // (elements outside the tensor read as zero) and completes the barrier's
 // transaction count.  Every thread then waits on the barrier's phase with a
 // bounded wait: after ~2 s of device time it gives up and reports a timeout
-// instead of spinning forever.
+// instead of waiting forever.
 #pragma once
 
 #include <cuda.h>
@@ -50,13 +50,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier; false after ~2 s (or 2^26 polls).
+// As mbar_try_wait, but a thread whose phase is not complete is suspended
+// in hardware until it completes or `ns` nanoseconds pass (no polling loop
+// competing for issue slots while a TMA load is in flight).
+__device__ __forceinline__ bool mbar_try_wait_for(uint64_t* bar, unsigned parity, unsigned ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier; false after ~2 s of device time
+// (or 2^26 suspended waits of at most 0.1 ms each).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   for (int i = 0; i < (1 << 26); ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    __nanosleep(64);
+    if (mbar_try_wait_for(bar, parity, 100000u)) return true;
     if (clock64() - t0 > 4000000000LL) break;
   }
   return false;

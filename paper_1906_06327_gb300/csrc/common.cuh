@@ -74,6 +74,10 @@ struct stream_args {
   const void* in;
   void* out;
   const void* coef;   // coef5<T>[coefficient lines][lt + 1]
+  // the same unfolded-form weights of complex float as three planes
+  // [m2, al, be][lt + 1][coefficient lines] (consecutive lines contiguous)
+  const float2* coefT;
+  int tlines;         // coefficient lines
   int len;            // N: stored points per line
   int lt;             // index of the converged table entry
   int nseg, seg_chunks, warm, halo;
@@ -164,8 +168,9 @@ struct sweep_shape {
   size_t smem;
 };
 
-cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis_coef& co,
-                          cudaStream_t s);
+// tableT: the planes of stream_args::coefT (complex float only), or null
+cudaError_t launch_tables(bool fp64, void* table, void* tableT, int nlines, int lt,
+                          const axis_coef& co, cudaStream_t s);
 // map: rows TMA map of the input buffer or null; omap: the swizzled
 // one-row-per-lane map of the output buffer (that form only) or null
 cudaError_t launch_sweep_x(bool fp64, bool imag, const stream_args& a, const sweep_shape& sh,

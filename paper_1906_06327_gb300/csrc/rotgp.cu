@@ -41,6 +41,7 @@ struct AxisPlan {
   int nlines = 0;       // lines with distinct coefficients (table rows)
   axis_coef co[2];      // [mode] 0 = real, 1 = imaginary
   void* table[2] = {nullptr, nullptr};
+  void* tableT[2] = {nullptr, nullptr};  // complex float: [m2, al, be][lt + 1][nlines]
   // launch plan of this axis' sweep
   long long lines = 0;  // lines solved per sweep
   int len = 0;          // points per line
@@ -334,11 +335,28 @@ int set_shape(rotgp_ctx* c, int a, int V, int C, int R, int wpb, long long nseg)
   return ROTGP_OK;
 }
 
+// Default shape of the one-line-per-lane TMA sweeps (complex float, once
+// their tensor maps exist): chunks of 8, a 5-slot ring, and segments so that
+// the 32-line units come to about 14 per SM (one wave of persistent warps).
+void lean_defaults(rotgp_ctx* c) {
+  if (c->fp64 || c->halo > 8) return;
+  for (int a = 0; a < c->grid.dim; ++a) {
+    AxisPlan& ap = c->axis[a];
+    if (!(a == 0 ? c->xmaps_ok && c->x_tma : c->smaps_ok)) continue;
+    const AxisPlan keep = ap;
+    const long long groups = (ap.lines + 31) / 32, nch = (ap.len + 7) / 8;
+    const long long nseg = std::max<long long>(
+        1, std::min<long long>(nch, (14LL * c->sm_count + groups / 2) / groups));
+    if (set_shape(c, a, 1, 8, 5, 1, nseg) != ROTGP_OK) ap = keep;
+  }
+}
+
 // Default launch plan of every sweep: complex float solves two lines per
 // lane in chunks of 8 (16 if the halo is longer), double one line in chunks
 // of 16 (64); a 3-slot ring; one warp per block, so that blocks of ~15 KB
 // pack each SM densely; and enough segments per line for about one wave of
-// resident warps.
+// resident warps.  Where the TMA maps exist, complex float takes the
+// one-line-per-lane forms instead (lean_defaults).
 int plan_axes(rotgp_ctx* c) {
   const size_t sm_bytes = 228 * 1024;
   for (int a = 0; a < c->grid.dim; ++a) {
@@ -397,6 +415,7 @@ int plan_axes(rotgp_ctx* c) {
     c->fuse_xy = false;
   }
   c->fuse_ok = c->fuse_ok && ax.stencil_ok && ay.stencil_ok;
+  lean_defaults(c);
   c->fuse_xy = c->fuse_xy && c->fuse_ok;
   return ROTGP_OK;
 }
@@ -555,8 +574,8 @@ int build_tables(rotgp_ctx* c) {
       ap.co[mode] = make_coef(a, mode, c->grid.h[a], c->phys.dt, c->phys.omega,
                               nlines_u0(c, a), nlines_du(c, a));
       Timed t(c, K_TABLES);
-      cudaError_t e = launch_tables(c->fp64, ap.table[mode], ap.nlines, c->lt, ap.co[mode],
-                                    c->stream);
+      cudaError_t e = launch_tables(c->fp64, ap.table[mode], ap.tableT[mode], ap.nlines, c->lt,
+                                    ap.co[mode], c->stream);
       if (e == cudaSuccess && ap.stencil_ok && ap.wtab[mode])
         e = launch_stencil_tables(ap.wtab[mode], ap.nlines, ap.sK, ap.sB,
                                   2 * ap.sB + 2 * ap.sK + 8, ap.co[mode], c->stream);
@@ -625,6 +644,8 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
   a.in = c->psi[c->cur];
   a.out = c->psi[1 - c->cur];
   a.coef = ap.table[mode];
+  a.coefT = static_cast<const float2*>(ap.tableT[mode]);
+  a.tlines = ap.nlines;
   a.len = ap.len;
   a.lt = c->lt;
   a.nseg = ap.nseg;
@@ -904,6 +925,10 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
   for (int a = 0; a < grid->dim && !rc; ++a)
     for (int m = 0; m < 2 && !rc; ++m)
       rc = dev_alloc(c, &c->axis[a].table[m], (size_t)c->axis[a].nlines * (c->lt + 1) * tab_elem);
+  for (int a = 0; a < grid->dim && !rc && !c->fp64; ++a)
+    for (int m = 0; m < 2 && !rc; ++m)
+      rc = dev_alloc(c, &c->axis[a].tableT[m],
+                     (size_t)3 * c->axis[a].nlines * (c->lt + 1) * sizeof(float2));
   for (int a = 0; a < grid->dim && !rc; ++a) {
     AxisPlan& ap = c->axis[a];
     if (!ap.stencil_ok) continue;
@@ -937,6 +962,7 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     if (e != cudaSuccess) rc = cuda_fail(c, e, "initialise buffers");
   }
   if (!rc) build_maps(c);
+  if (!rc) lean_defaults(c);
   if (!rc) rc = build_tables(c);
   if (!rc) {
     e = cudaStreamSynchronize(c->stream);

@@ -286,25 +286,29 @@ __device__ __forceinline__ void cmac(cacc& c, const float2& wr, const float2& wi
 __device__ __forceinline__ float2 cfin(const cacc& c) {
   return make_float2(c.a.x - c.b.y, c.a.y + c.b.x);
 }
-// Table coefficients of positions p0 .. p0 + C - 1 of one line (entries past
-// the table length are the converged ones), all loads issued together ahead
-// of the recurrence that uses them, which would otherwise wait on each load
-// in turn (the table path of the line start and of a ragged line end).
+// Unfolded-form weights of positions p0 .. p0 + C - 1 of line li from the
+// planes of stream_args::coefT (entries past the table length are the
+// converged ones).  The loads of a chunk are issued together, ahead of the
+// recurrence that would otherwise wait on each in turn; the lanes of a warp
+// read consecutive lines, so every load is one or two contiguous segments.
+__device__ __forceinline__ float2 coef_plane(const float2* tab, int tl, int lt, int f, int p,
+                                             int li) {
+  return __ldg(tab + ((size_t)f * (lt + 1) + min(p, lt)) * tl + li);
+}
 template <int C>
-__device__ __forceinline__ void table_fwd(const coef5<float>* crow, int p0, int lt,
+__device__ __forceinline__ void table_fwd(const float2* tab, int tl, int lt, int li, int p0,
                                           float2 (&m2)[C], float2 (&al)[C]) {
 #pragma unroll
   for (int r = 0; r < C; ++r) {
-    const coef5<float>* k = crow + min(p0 + r, lt);
-    m2[r] = __ldg(reinterpret_cast<const float2*>(&k->m2));
-    al[r] = __ldg(reinterpret_cast<const float2*>(&k->al));
+    m2[r] = coef_plane(tab, tl, lt, 0, p0 + r, li);
+    al[r] = coef_plane(tab, tl, lt, 1, p0 + r, li);
   }
 }
 template <int C>
-__device__ __forceinline__ void table_be(const coef5<float>* crow, int p0, int lt,
+__device__ __forceinline__ void table_be(const float2* tab, int tl, int lt, int li, int p0,
                                          float2 (&be)[C]) {
 #pragma unroll
-  for (int r = 0; r < C; ++r) be[r] = __ldg(reinterpret_cast<const float2*>(&crow[min(p0 + r, lt)].be));
+  for (int r = 0; r < C; ++r) be[r] = coef_plane(tab, tl, lt, 2, p0 + r, li);
 }
 
 // a complex weight as the two duplicated pairs (wr, wr), (wi, wi)

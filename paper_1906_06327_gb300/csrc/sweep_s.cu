@@ -35,7 +35,7 @@ template <class T>
 __device__ __forceinline__ cpx<T> dcast(dcx a) { return mk<T>((T)a.x, (T)a.y); }
 
 template <class T>
-__global__ void k_tables(coef5<T>* tab, int nlines, int lt, axis_coef co) {
+__global__ void k_tables(coef5<T>* tab, float2* tabT, int nlines, int lt, axis_coef co) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= nlines) return;
   const double u = co.u0 + (double)l * co.du;
@@ -58,6 +58,15 @@ __global__ void k_tables(coef5<T>* tab, int nlines, int lt, axis_coef co) {
     t[p].al = dcast<T>({-mam.x, -mam.y});
     t[p].be = dcast<T>({-c.x, -c.y});
     t[p].m2 = dcast<T>({2.0 * m.x, 2.0 * m.y});
+  }
+  if (tabT) {
+    const size_t P = (size_t)(lt + 1) * nlines;
+    for (int p = 0; p <= lt; ++p) {
+      const size_t i = (size_t)p * nlines + l;
+      tabT[i] = make_float2((float)t[p].m2.x, (float)t[p].m2.y);
+      tabT[P + i] = make_float2((float)t[p].al.x, (float)t[p].al.y);
+      tabT[2 * P + i] = make_float2((float)t[p].be.x, (float)t[p].be.y);
+    }
   }
 }
 
@@ -349,13 +358,15 @@ __global__ void __launch_bounds__(128) k_sweep_strided2(const stream_args a) {
 }
 
 // --------------------------------------------------------------- launchers
-cudaError_t launch_tables(bool fp64, void* table, int nlines, int lt, const axis_coef& co,
-                          cudaStream_t s) {
+cudaError_t launch_tables(bool fp64, void* table, void* tableT, int nlines, int lt,
+                          const axis_coef& co, cudaStream_t s) {
   const int threads = 128, blocks = (nlines + threads - 1) / threads;
   if (fp64)
-    k_tables<double><<<blocks, threads, 0, s>>>(static_cast<coef5<double>*>(table), nlines, lt, co);
+    k_tables<double><<<blocks, threads, 0, s>>>(static_cast<coef5<double>*>(table), nullptr,
+                                                nlines, lt, co);
   else
-    k_tables<float><<<blocks, threads, 0, s>>>(static_cast<coef5<float>*>(table), nlines, lt, co);
+    k_tables<float><<<blocks, threads, 0, s>>>(static_cast<coef5<float>*>(table),
+                                               static_cast<float2*>(tableT), nlines, lt, co);
   return cudaGetLastError();
 }
 
@@ -524,15 +535,13 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
     const int N = a.len, nch = (N + C - 1) / C, lt = a.lt;
     const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
     const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
-    const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) +
-                               (size_t)(a.coef_mode == 1 && act ? x : 0) * (lt + 1);
+    const int li = a.coef_mode == 1 && act ? x : 0;  // the line's coefficient line
+    const float2* tab = a.coefT;
+    const int tl = a.tlines;
     float2 M2R, M2I, ALR, ALI, BER, BEI;
-    {
-      const coef5<float> cf = crow[lt];
-      wsplit(make_float2(cf.m2.x, cf.m2.y), M2R, M2I);
-      wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
-      wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
-    }
+    wsplit(coef_plane(tab, tl, lt, 0, lt, li), M2R, M2I);
+    wsplit(coef_plane(tab, tl, lt, 1, lt, li), ALR, ALI);
+    wsplit(coef_plane(tab, tl, lt, 2, lt, li), BER, BEI);
     const float2 NEG1 = make_float2(-1.f, -1.f);
     // d_p = m2 psi_p + al d_{p-1}
     auto fwd = [](float2 mr, float2 mi, float2 lr, float2 li, float2 psi, float2 d) -> float2 {
@@ -587,8 +596,8 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
             cur[r] = d;
           }
         } else {
-float2 km[C], kl[C];
-          table_fwd<C>(crow, p0, lt, km, kl);
+          float2 km[C], kl[C];
+          table_fwd<C>(tab, tl, lt, li, p0, km, kl);
 #pragma unroll
           for (int r = 0; r < C; ++r) {
             float2 mr, mi, lr, li;
@@ -610,7 +619,7 @@ float2 km[C], kl[C];
             for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
           } else {
             float2 kb[C];
-            table_be<C>(crow, p0, lt, kb);
+            table_be<C>(tab, tl, lt, li, p0, kb);
 #pragma unroll
             for (int h = C - 1; h >= 0; --h)
               if (p0 + h < N) {
@@ -634,7 +643,7 @@ float2 km[C], kl[C];
           }
         } else {
           float2 kb[C];
-          table_be<C>(crow, p0, lt, kb);
+          table_be<C>(tab, tl, lt, li, p0, kb);
 #pragma unroll
           for (int r = C - 1; r >= 0; --r)
             if (p0 + r < N) {

@@ -532,14 +532,13 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
     const int qo0 = sg * a.seg_chunks, qo1 = min(nch, qo0 + a.seg_chunks);
     const int qa = max(0, qo0 - a.warm), qb = min(nch, qo1 + 1);
     const int jj = act ? (int)(row % a.ny) : 0, kk = act ? (int)(row / a.ny) : 0;
-    const coef5<float>* crow = static_cast<const coef5<float>*>(a.coef) + (size_t)jj * (lt + 1);
+    const int li = jj;  // the line's coefficient line
+    const float2* tab = a.coefT;
+    const int tl = a.tlines;
     float2 M2R, M2I, ALR, ALI, BER, BEI;
-    {
-      const coef5<float> cf = crow[lt];
-      wsplit(make_float2(cf.m2.x, cf.m2.y), M2R, M2I);
-      wsplit(make_float2(cf.al.x, cf.al.y), ALR, ALI);
-      wsplit(make_float2(cf.be.x, cf.be.y), BER, BEI);
-    }
+    wsplit(coef_plane(tab, tl, lt, 0, lt, li), M2R, M2I);
+    wsplit(coef_plane(tab, tl, lt, 1, lt, li), ALR, ALI);
+    wsplit(coef_plane(tab, tl, lt, 2, lt, li), BER, BEI);
     const float2 NEG1 = make_float2(-1.f, -1.f);
     const float yv = (float)(a.y0 + (double)jj * a.hy), zv = (float)(a.z0 + (double)kk * a.hz);
     const float vyz = (float)a.hnu2 * yv * yv + (float)a.hlam2 * zv * zv;
@@ -615,8 +614,8 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
             cur[r] = d;
           }
         } else {
-  float2 km[C], kl[C];
-          table_fwd<C>(crow, p0, lt, km, kl);
+          float2 km[C], kl[C];
+          table_fwd<C>(tab, tl, lt, li, p0, km, kl);
 #pragma unroll
           for (int r = 0; r < C; ++r) {
             float2 mr, mi, lr, li;
@@ -642,7 +641,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
             for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
           } else {
             float2 kb[C];
-            table_be<C>(crow, p0, lt, kb);
+            table_be<C>(tab, tl, lt, li, p0, kb);
 #pragma unroll
             for (int h = C - 1; h >= 0; --h)
               if (p0 + h < N) {
@@ -665,7 +664,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
           }
         } else {
           float2 kb[C];
-          table_be<C>(crow, p0, lt, kb);
+          table_be<C>(tab, tl, lt, li, p0, kb);
 #pragma unroll
           for (int u = U - 1; u >= 0; --u) {
             const float4 t = *unit(sp, u);

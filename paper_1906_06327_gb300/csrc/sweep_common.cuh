@@ -26,6 +26,7 @@
 #pragma once
 
 #include "common.cuh"
+#include <cstdint>
 
 namespace rotgp {
 
@@ -291,24 +292,31 @@ __device__ __forceinline__ float2 cfin(const cacc& c) {
 // converged ones).  The loads of a chunk are issued together, ahead of the
 // recurrence that would otherwise wait on each in turn; the lanes of a warp
 // read consecutive lines, so every load is one or two contiguous segments.
+// The loads carry an L2 policy (evict_last: the planes are read by every
+// sweep, between which the state streams through L2).
 __device__ __forceinline__ float2 coef_plane(const float2* tab, int tl, int lt, int f, int p,
-                                             int li) {
-  return __ldg(tab + ((size_t)f * (lt + 1) + min(p, lt)) * tl + li);
+                                             int li, uint64_t pol) {
+  const float2* a = tab + ((size_t)f * (lt + 1) + min(p, lt)) * tl + li;
+  float2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(v.x), "=f"(v.y)
+               : "l"(a), "l"(pol));
+  return v;
 }
 template <int C>
 __device__ __forceinline__ void table_fwd(const float2* tab, int tl, int lt, int li, int p0,
-                                          float2 (&m2)[C], float2 (&al)[C]) {
+                                          uint64_t pol, float2 (&m2)[C], float2 (&al)[C]) {
 #pragma unroll
   for (int r = 0; r < C; ++r) {
-    m2[r] = coef_plane(tab, tl, lt, 0, p0 + r, li);
-    al[r] = coef_plane(tab, tl, lt, 1, p0 + r, li);
+    m2[r] = coef_plane(tab, tl, lt, 0, p0 + r, li, pol);
+    al[r] = coef_plane(tab, tl, lt, 1, p0 + r, li, pol);
   }
 }
 template <int C>
 __device__ __forceinline__ void table_be(const float2* tab, int tl, int lt, int li, int p0,
-                                         float2 (&be)[C]) {
+                                         uint64_t pol, float2 (&be)[C]) {
 #pragma unroll
-  for (int r = 0; r < C; ++r) be[r] = coef_plane(tab, tl, lt, 2, p0 + r, li);
+  for (int r = 0; r < C; ++r) be[r] = coef_plane(tab, tl, lt, 2, p0 + r, li, pol);
 }
 
 // a complex weight as the two duplicated pairs (wr, wr), (wi, wi)

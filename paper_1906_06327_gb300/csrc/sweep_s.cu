@@ -519,6 +519,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
   // and visible past this wait, and nothing above touched global memory
   griddep_launch_dependents();
   griddep_wait();
+  const uint64_t pol_first = l2_evict_first(), pol_last = l2_evict_last();
   unsigned ph = 0;  // phase parity of every slot's barrier, kept from unit to unit
   bool good = true;
   // units (a patch of 32 lines and one segment of them) in a fixed
@@ -539,9 +540,9 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
     const float2* tab = a.coefT;
     const int tl = a.tlines;
     float2 M2R, M2I, ALR, ALI, BER, BEI;
-    wsplit(coef_plane(tab, tl, lt, 0, lt, li), M2R, M2I);
-    wsplit(coef_plane(tab, tl, lt, 1, lt, li), ALR, ALI);
-    wsplit(coef_plane(tab, tl, lt, 2, lt, li), BER, BEI);
+    wsplit(coef_plane(tab, tl, lt, 0, lt, li, pol_last), M2R, M2I);
+    wsplit(coef_plane(tab, tl, lt, 1, lt, li, pol_last), ALR, ALI);
+    wsplit(coef_plane(tab, tl, lt, 2, lt, li, pol_last), BER, BEI);
     const float2 NEG1 = make_float2(-1.f, -1.f);
     // d_p = m2 psi_p + al d_{p-1}
     auto fwd = [](float2 mr, float2 mi, float2 lr, float2 li, float2 psi, float2 d) -> float2 {
@@ -564,7 +565,8 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
       coords(q, c1, c2);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
-      tma_load_3d(ring + (size_t)sl * SLOT, &map, 64 * gx, c1, c2, &bar[sl]);
+      tma_load_3d_hint(ring + (size_t)sl * SLOT, &map, 64 * gx, c1, c2, &bar[sl],
+                       pol_first);
     };
     if (lane == 0) {
       bulk_wait_read<0>();  // the previous unit's stores have left their slots
@@ -597,7 +599,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
           }
         } else {
           float2 km[C], kl[C];
-          table_fwd<C>(tab, tl, lt, li, p0, km, kl);
+          table_fwd<C>(tab, tl, lt, li, p0, pol_last, km, kl);
 #pragma unroll
           for (int r = 0; r < C; ++r) {
             float2 mr, mi, lr, li;
@@ -619,7 +621,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
             for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
           } else {
             float2 kb[C];
-            table_be<C>(tab, tl, lt, li, p0, kb);
+            table_be<C>(tab, tl, lt, li, p0, pol_last, kb);
 #pragma unroll
             for (int h = C - 1; h >= 0; --h)
               if (p0 + h < N) {
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
           }
         } else {
           float2 kb[C];
-          table_be<C>(tab, tl, lt, li, p0, kb);
+          table_be<C>(tab, tl, lt, li, p0, pol_last, kb);
 #pragma unroll
           for (int r = C - 1; r >= 0; --r)
             if (p0 + r < N) {

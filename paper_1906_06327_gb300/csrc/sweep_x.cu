@@ -515,6 +515,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
   // and visible past this wait, and nothing above touched global memory
   griddep_launch_dependents();
   griddep_wait();
+  const uint64_t pol_first = l2_evict_first(), pol_last = l2_evict_last();
   unsigned ph = 0;  // phase parity of every slot's barrier, kept from unit to unit
   bool good = true;
   // units (32 rows and one segment of them) in a fixed round-robin order
@@ -536,9 +537,9 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
     const float2* tab = a.coefT;
     const int tl = a.tlines;
     float2 M2R, M2I, ALR, ALI, BER, BEI;
-    wsplit(coef_plane(tab, tl, lt, 0, lt, li), M2R, M2I);
-    wsplit(coef_plane(tab, tl, lt, 1, lt, li), ALR, ALI);
-    wsplit(coef_plane(tab, tl, lt, 2, lt, li), BER, BEI);
+    wsplit(coef_plane(tab, tl, lt, 0, lt, li, pol_last), M2R, M2I);
+    wsplit(coef_plane(tab, tl, lt, 1, lt, li, pol_last), ALR, ALI);
+    wsplit(coef_plane(tab, tl, lt, 2, lt, li, pol_last), BER, BEI);
     const float2 NEG1 = make_float2(-1.f, -1.f);
     const float yv = (float)(a.y0 + (double)jj * a.hy), zv = (float)(a.z0 + (double)kk * a.hz);
     const float vyz = (float)a.hnu2 * yv * yv + (float)a.hlam2 * zv * zv;
@@ -575,7 +576,8 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
     auto issue = [&](int q, int sl) {  // lane 0
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
-      tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
+      tma_load_2d_hint(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl],
+                       pol_first);
     };
     if (lane == 0) {
       bulk_wait_read<0>();  // the previous unit's stores have left their slots
@@ -615,7 +617,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
           }
         } else {
           float2 km[C], kl[C];
-          table_fwd<C>(tab, tl, lt, li, p0, km, kl);
+          table_fwd<C>(tab, tl, lt, li, p0, pol_last, km, kl);
 #pragma unroll
           for (int r = 0; r < C; ++r) {
             float2 mr, mi, lr, li;
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
             for (int h = C - 1; h >= 0; --h) z = bstep(BER, BEI, z, cur[h]);
           } else {
             float2 kb[C];
-            table_be<C>(tab, tl, lt, li, p0, kb);
+            table_be<C>(tab, tl, lt, li, p0, pol_last, kb);
 #pragma unroll
             for (int h = C - 1; h >= 0; --h)
               if (p0 + h < N) {
@@ -664,7 +666,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
           }
         } else {
           float2 kb[C];
-          table_be<C>(tab, tl, lt, li, p0, kb);
+          table_be<C>(tab, tl, lt, li, p0, pol_last, kb);
 #pragma unroll
           for (int u = U - 1; u >= 0; --u) {
             const float4 t = *unit(sp, u);

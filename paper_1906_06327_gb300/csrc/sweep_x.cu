@@ -559,6 +559,18 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
         return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
       }
     };
+    // imaginary time: the factor sc exp(-dt (V + g sc^2 |v|^2)) of a raw
+    // point v as one base-2 exponential of a quadratic in x and |v|^2, the
+    // pending scale folded in as log2(sc)
+    const float L2E = 1.4426950408889634f;
+    const float k1 = -dt * gg * sc * sc * L2E, kx = -dt * hg2 * L2E;
+    const float k0 = fmaf(-dt * L2E, vyz, log2f(sc));
+    auto h1i = [&](float2 v, float x) -> float2 {
+      const float t = fmaf(k1, fmaf(v.x, v.x, v.y * v.y), fmaf(kx * x, x, k0));
+      float f;
+      asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"(t));
+      return __fmul2_rn(make_float2(f, f), v);
+    };
     auto fwd = [](float2 mr, float2 mi, float2 lr, float2 li, float2 psi, float2 d) -> float2 {
       float2 A = __fmul2_rn(mr, psi), B = __fmul2_rn(mi, psi);
       A = __ffma2_rn(lr, d, A);
@@ -602,12 +614,18 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
         }
         ph ^= 1u << sq;
         const int p0 = q * C;
+        const float xp0 = fmaf((float)p0, hx, xs);  // x of the chunk's first point
         float2 w[C];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const float4 t = *unit(sq, u);
-          w[2 * u] = h1(make_float2(t.x, t.y), p0 + 2 * u);
-          w[2 * u + 1] = h1(make_float2(t.z, t.w), p0 + 2 * u + 1);
+          if (IMAG) {
+            w[2 * u] = h1i(make_float2(t.x, t.y), fmaf((float)(2 * u), hx, xp0));
+            w[2 * u + 1] = h1i(make_float2(t.z, t.w), fmaf((float)(2 * u + 1), hx, xp0));
+          } else {
+            w[2 * u] = h1(make_float2(t.x, t.y), p0 + 2 * u);
+            w[2 * u + 1] = h1(make_float2(t.z, t.w), p0 + 2 * u + 1);
+          }
         }
         if (p0 >= lt && p0 + C <= N) {
 #pragma unroll

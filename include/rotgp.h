@@ -181,7 +181,11 @@ int rotgp_info(const rotgp_ctx* ctx, rotgp_solver_info* out);
  * per thread, and 8 or 16 (TMA forms, even N_x) or 16 or 64 with one;
  * double takes 16 or 64), ring slots (3 or 4; 5 or 6 too in the TMA forms
  * with one line per thread and chunk 8), warps per block (1..8) and
- * segments each line is split into (clamped to the number of chunks).  Changes speed only: every shape gives results
+ * segments each line is split into (clamped to the number of chunks).
+ * The one-line-per-thread TMA forms (chunk 8 or 16) solve the unfolded
+ * system psi' = 2 A^-1 psi - psi and serve imaginary-time steps; real-time
+ * steps of an axis so tuned run the default two-lines-per-thread form, whose
+ * folded weights keep the CN map's norm to float rounding.  Changes speed only: every shape gives results
  * equal up to the truncation bound of the chunked line solver.  Used by the
  * autotuner.  ROTGP_EINVAL for a shape that is not built or does not fit. */
 int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring,

@@ -47,6 +47,15 @@ struct AxisPlan {
   int len = 0;          // points per line
   int nseg = 1, seg_chunks = 1, warm = 1;
   sweep_shape sh{};
+  // real-time launch plan when sh is a one-line-per-lane TMA (unfolded)
+  // shape: that form rounds 2 A^-1 psi before subtracting psi, which doubles
+  // the effect of the rounded weights and drifts the real-time norm; real
+  // time keeps the folded two-lines-per-lane form
+  struct {
+    bool set = false;
+    int nseg = 1, seg_chunks = 1, warm = 1;
+    sweep_shape sh{};
+  } rt;
   // banded-inverse stencil (complex float): taps K, end rows B, weights [mode]
   bool stencil_ok = false;  // stencil form available for this axis
   bool use_stencil = false;
@@ -344,6 +353,13 @@ void lean_defaults(rotgp_ctx* c) {
     AxisPlan& ap = c->axis[a];
     if (!(a == 0 ? c->xmaps_ok && c->x_tma : c->smaps_ok)) continue;
     const AxisPlan keep = ap;
+    if (ap.sh.V != 1) {
+      ap.rt.set = true;
+      ap.rt.nseg = ap.nseg;
+      ap.rt.seg_chunks = ap.seg_chunks;
+      ap.rt.warm = ap.warm;
+      ap.rt.sh = ap.sh;
+    }
     const long long groups = (ap.lines + 31) / 32, nch = (ap.len + 7) / 8;
     const long long nseg = std::max<long long>(
         1, std::min<long long>(nch, (14LL * c->sm_count + groups / 2) / groups));
@@ -639,7 +655,14 @@ int xy_pass(rotgp_ctx* c, bool imag) {
 
 int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
   const int mode = imag ? 1 : 0;
-  const AxisPlan& ap = c->axis[axis];
+  AxisPlan ap = c->axis[axis];
+  if (!imag && !c->fp64 && ap.sh.V == 1 && (ap.sh.C == 8 || ap.sh.C == 16) && ap.rt.set &&
+      (axis == 0 ? c->xmaps_ok && c->x_tma : c->smaps_ok)) {
+    ap.nseg = ap.rt.nseg;
+    ap.seg_chunks = ap.rt.seg_chunks;
+    ap.warm = ap.rt.warm;
+    ap.sh = ap.rt.sh;
+  }
   stream_args a{};
   a.in = c->psi[c->cur];
   a.out = c->psi[1 - c->cur];

@@ -363,10 +363,10 @@ class Batch:
     def autotune(self, steps: int = 5):
         self._check(self._lib.rotgp_batch_autotune(self._h, int(steps)))
 
-    def step_imag(self, n: int, graph: bool = True):
+    def step_imag(self, n: int, graph: bool = False):
         self._check(self._lib.rotgp_batch_step(self._h, int(n), 1, int(bool(graph))))
 
-    def step_real(self, n: int, graph: bool = True):
+    def step_real(self, n: int, graph: bool = False):
         self._check(self._lib.rotgp_batch_step(self._h, int(n), 0, int(bool(graph))))
 
     def sync(self):
@@ -377,7 +377,7 @@ class Batch:
         self._check(self._lib.rotgp_batch_observables(self._h, out))
         return [o.as_dict() for o in out]
 
-    def converge(self, rel_tol: float, check_every: int, max_steps: int, graph: bool = True):
+    def converge(self, rel_tol: float, check_every: int, max_steps: int, graph: bool = False):
         """Returns (steps per instance, converged flags)."""
         steps = (ctypes.c_longlong * self.count)()
         conv = (ctypes.c_int * self.count)()

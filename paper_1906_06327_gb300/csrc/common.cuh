@@ -137,7 +137,7 @@ struct obs_args {
   double hx, hy, hz, x0, y0, z0;
   double hgam2, hnu2, hlam2, g, omega;
   const double* scale;
-  int rows_per_block;  // x rows (j, k) reduced by one block
+  int zchunk;          // z planes per work item (tiles of 32 x 8 columns)
   double* partials;
   unsigned int* counter;
   double* result;  // NOBS doubles

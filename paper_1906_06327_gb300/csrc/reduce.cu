@@ -96,9 +96,18 @@ __device__ void combine_all(const double* partials, double* fin) {
 //       (-f2 + 16 f1 - 30 f0 + 16 f-1 - f-2)/(12 h^2), first derivative
 //       (-f2 + 8 f1 - 8 f-1 + f-2)/(12 h); points beyond the grid are zero)
 //   q13 max |psi|^2
+// The state is read once: a block owns tiles of 32 x 8 columns (x, y) and a
+// range of z; each thread walks its column in z with the five points z-2 ..
+// z+2 in registers, and the plane z is staged in shared memory with a halo
+// of 2 in x and y for the x and y differences (a star stencil: no corners).
+// Work items (tile, z range) are taken grid-stride.
+constexpr int kObsTX = 32, kObsTY = 8;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
   using C = cpx<T>;
+  constexpr int TX = kObsTX, TY = kObsTY, WX = TX + 4, WY = TY + 4;
+  __shared__ C tile[2][WY][WX];
   const C* psi = static_cast<const C*>(a.psi);
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long long plane = (long long)nx * ny;
@@ -107,79 +116,113 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
   const T ihz2 = a.dim == 3 ? (T)(1.0 / (a.hz * a.hz)) : (T)0;
   const T i2hx = (T)(0.5 / a.hx), i2hy = (T)(0.5 / a.hy);
   const T om = (T)a.omega, g = (T)a.g;
-  // per-thread sums over a short strip of sites in the working precision,
-  // promoted to double for the block and grid reduction
+  const T c12x = ihx2 / (T)12, c12y = ihy2 / (T)12, c12z = ihz2 / (T)12;
+  const T i12hx = (T)(0.5 / a.hx / 6.0), i12hy = (T)(0.5 / a.hy / 6.0);
+  // coordinates and potential constants in the working precision, once:
+  // no conversion from double inside the site loops
+  const T x0 = (T)a.x0, y0 = (T)a.y0, z0 = (T)a.z0, hx = (T)a.hx, hy = (T)a.hy;
+  const T hz = a.dim == 3 ? (T)a.hz : (T)0;
+  const T hgam2 = (T)a.hgam2, hnu2 = (T)a.hnu2, hlam2 = (T)a.hlam2;
+  const bool d3 = a.dim == 3;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int tiles_x = (nx + TX - 1) / TX, tiles_y = (ny + TY - 1) / TY;
+  const int zlen = a.zchunk, zparts = (nz + zlen - 1) / zlen;
+  const long long items = (long long)tiles_x * tiles_y * zparts;
+  // a point of the state (scaled), zero outside the stored grid
+  auto at = [&](int i, int j, int k) -> C {
+    if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz) return mk<T>(0, 0);
+    return s * psi[(long long)k * plane + (long long)j * nx + i];
+  };
+  // per-thread sums in the working precision, promoted to double for the
+  // block and grid reduction
   T t[NQ];
 #pragma unroll
   for (int v = 0; v < NQ; ++v) t[v] = 0;
-  const int nrows = ny * nz;
-  const int r0 = blockIdx.x * a.rows_per_block, r1 = min(nrows, r0 + a.rows_per_block);
-  for (int row = r0; row < r1; ++row) {
-    const int j = row % ny, k = row / ny;
-    if (j == 0 || (a.dim == 3 && k == 0)) continue;
-    const T y = (T)(a.y0 + (double)j * a.hy);
-    const T z = a.dim == 3 ? (T)(a.z0 + (double)k * a.hz) : (T)0;
-    const T vyz = (T)a.hnu2 * y * y + (T)a.hlam2 * z * z;
-    const C* rp = psi + (long long)row * nx;
-    const bool has_yp = j + 1 < ny, has_zp = a.dim == 3 && k + 1 < nz;
-    const bool has_yp2 = j + 2 < ny, has_ym2 = j >= 2;
-    const bool has_zp2 = a.dim == 3 && k + 2 < nz, has_zm2 = a.dim == 3 && k >= 2;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      if (i == 0) continue;
-      const T x = (T)(a.x0 + (double)i * a.hx);
-      const T V = (T)a.hgam2 * x * x + vyz;
-      const C c = s * rp[i];
-      const C xp = i + 1 < nx ? s * rp[i + 1] : mk<T>(0, 0);
-      const C xm = s * rp[i - 1];
-      const C yp = has_yp ? s * rp[i + nx] : mk<T>(0, 0);
-      const C ym = s * rp[i - nx];
-      C lap = ihx2 * (xp + xm - (T)2 * c) + ihy2 * (yp + ym - (T)2 * c);
-      if (a.dim == 3) {
-        const C zp = has_zp ? s * rp[i + plane] : mk<T>(0, 0);
-        const C zm = s * rp[i - plane];
-        lap = lap + ihz2 * (zp + zm - (T)2 * c);
-      }
-      const C dx = i2hx * (xp - xm), dy = i2hy * (yp - ym);
-      const T re = c.x, im = c.y, dens = re * re + im * im;
-      const T hr = (T)-0.5 * lap.x + V * re + om * (y * dx.y - x * dy.y);
-      const T hi = (T)-0.5 * lap.y + V * im + om * (-(y * dx.x) + x * dy.x);
-      // -Omega L_z psi = -Omega i (y D_x - x D_y) psi
-      const C lz = y * dx - x * dy;  // L_z psi / i
-      const C hlin = mk<T>((T)-0.5 * lap.x + V * c.x + om * lz.y,
-                           (T)-0.5 * lap.y + V * c.y - om * lz.x);
-      t[0] += dens;
-      t[1] += re * re;
-      t[2] += im * im;
-      t[3] += re * hr;
-      t[4] += g * dens * re * re;
-      t[5] += im * hi;
-      t[6] += g * dens * im * im;
-      t[7] += re * hlin.x + im * hlin.y;
-      t[8] += g * dens * dens;
-      t[9] += x * x * dens;
-      t[10] += y * y * dens;
-      t[11] += z * z * dens;
-      {
-        const C z0 = mk<T>(0, 0);
-        const C xp2 = i + 2 < nx ? s * rp[i + 2] : z0, xm2 = i >= 2 ? s * rp[i - 2] : z0;
-        const C yp2 = has_yp2 ? s * rp[i + 2 * nx] : z0, ym2 = has_ym2 ? s * rp[i - 2 * nx] : z0;
-        const T c12x = ihx2 / (T)12, c12y = ihy2 / (T)12;
+  int buf = 0;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int zp_ = (int)(it % zparts);
+    const long long tt = it / zparts;
+    const int bx = (int)(tt % tiles_x), by = (int)(tt / tiles_x);
+    const int i = bx * TX + tx, j = by * TY + ty;
+    const int k0 = zp_ * zlen, k1 = min(nz, k0 + zlen);
+    const T x = x0 + (T)i * hx;
+    const T y = y0 + (T)j * hy;
+    const T xxv = hgam2 * x * x + hnu2 * y * y;
+    T kf = (T)k0;  // the plane index as a number, advanced per plane
+    // the column's window z-2 .. z+2
+    C w[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) w[d] = at(i, j, k0 - 2 + d);
+    // this thread's halo points of a plane (at most one in x, one in y)
+    const bool hxl = tx < 2, hxr = tx >= TX - 2, hyl = ty < 2, hyr = ty >= TY - 2;
+    const int hxi = hxl ? bx * TX - 2 + tx : bx * TX + tx + 2;
+    const int hyj = hyl ? by * TY - 2 + ty : by * TY + ty + 2;
+    auto halo_x = [&](int k) { return (hxl || hxr) ? at(hxi, j, k) : mk<T>(0, 0); };
+    auto halo_y = [&](int k) { return (hyl || hyr) ? at(i, hyj, k) : mk<T>(0, 0); };
+    C hxv = halo_x(k0), hyv = halo_y(k0);
+    for (int k = k0; k < k1; ++k) {
+      // the next plane's points are requested before this plane is used
+      const C wn = at(i, j, k + 3);
+      const C hxn = k + 1 < k1 ? halo_x(k + 1) : mk<T>(0, 0);
+      const C hyn = k + 1 < k1 ? halo_y(k + 1) : mk<T>(0, 0);
+      // stage the plane: centre from the window, halo strips
+      tile[buf][ty + 2][tx + 2] = w[2];
+      if (hxl) tile[buf][ty + 2][tx] = hxv;
+      if (hxr) tile[buf][ty + 2][tx + 4] = hxv;
+      if (hyl) tile[buf][ty][tx + 2] = hyv;
+      if (hyr) tile[buf][ty + 4][tx + 2] = hyv;
+      __syncthreads();
+      const bool interior = i >= 1 && i < nx && j >= 1 && j < ny && (!d3 || k >= 1);
+      if (interior) {
+        const C c = w[2];
+        const C xp = tile[buf][ty + 2][tx + 3], xm = tile[buf][ty + 2][tx + 1];
+        const C xp2 = tile[buf][ty + 2][tx + 4], xm2 = tile[buf][ty + 2][tx];
+        const C yp = tile[buf][ty + 3][tx + 2], ym = tile[buf][ty + 1][tx + 2];
+        const C yp2 = tile[buf][ty + 4][tx + 2], ym2 = tile[buf][ty][tx + 2];
+        const C zp = w[3], zm = w[1], zp2 = w[4], zm2 = w[0];
+        const T z = z0 + kf * hz;
+        const T V = xxv + hlam2 * z * z;
+        C lap = ihx2 * (xp + xm - (T)2 * c) + ihy2 * (yp + ym - (T)2 * c);
+        if (d3) lap = lap + ihz2 * (zp + zm - (T)2 * c);
+        const C dx = i2hx * (xp - xm), dy = i2hy * (yp - ym);
+        const T re = c.x, im = c.y, dens = re * re + im * im;
+        const T hr = (T)-0.5 * lap.x + V * re + om * (y * dx.y - x * dy.y);
+        const T hi = (T)-0.5 * lap.y + V * im + om * (-(y * dx.x) + x * dy.x);
+        // -Omega L_z psi = -Omega i (y D_x - x D_y) psi
+        const C lz = y * dx - x * dy;  // L_z psi / i
+        const C hlin = mk<T>((T)-0.5 * lap.x + V * c.x + om * lz.y,
+                             (T)-0.5 * lap.y + V * c.y - om * lz.x);
+        t[0] += dens;
+        t[1] += re * re;
+        t[2] += im * im;
+        t[3] += re * hr;
+        t[4] += g * dens * re * re;
+        t[5] += im * hi;
+        t[6] += g * dens * im * im;
+        t[7] += re * hlin.x + im * hlin.y;
+        t[8] += g * dens * dens;
+        t[9] += x * x * dens;
+        t[10] += y * y * dens;
+        t[11] += z * z * dens;
         C lap4 = c12x * ((T)16 * (xp + xm) - xp2 - xm2 - (T)30 * c) +
                  c12y * ((T)16 * (yp + ym) - yp2 - ym2 - (T)30 * c);
-        if (a.dim == 3) {
-          const C zp = has_zp ? s * rp[i + plane] : z0, zm = s * rp[i - plane];
-          const C zp2 = has_zp2 ? s * rp[i + 2 * plane] : z0;
-          const C zm2 = has_zm2 ? s * rp[i - 2 * plane] : z0;
-          lap4 = lap4 + (ihz2 / (T)12) * ((T)16 * (zp + zm) - zp2 - zm2 - (T)30 * c);
-        }
-        const C dx4 = (i2hx / (T)6) * ((T)8 * (xp - xm) - xp2 + xm2);
-        const C dy4 = (i2hy / (T)6) * ((T)8 * (yp - ym) - yp2 + ym2);
+        if (d3) lap4 = lap4 + c12z * ((T)16 * (zp + zm) - zp2 - zm2 - (T)30 * c);
+        const C dx4 = i12hx * ((T)8 * (xp - xm) - xp2 + xm2);
+        const C dy4 = i12hy * ((T)8 * (yp - ym) - yp2 + ym2);
         const C lz4 = y * dx4 - x * dy4;
         t[12] += re * ((T)-0.5 * lap4.x + V * c.x + om * lz4.y) +
                  im * ((T)-0.5 * lap4.y + V * c.y - om * lz4.x);
+        t[13] = t[13] > dens ? t[13] : dens;
       }
-      t[13] = t[13] > dens ? t[13] : dens;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) w[d] = w[d + 1];
+      w[4] = wn;
+      hxv = hxn;
+      hyv = hyn;
+      kf += (T)1;
+      buf ^= 1;  // the other buffer is free: every thread is past this plane's barrier
     }
+    __syncthreads();  // the next item restages both buffers
   }
   double q[NQ];
 #pragma unroll

@@ -1171,11 +1171,17 @@ int rotgp_observables(rotgp_ctx* c, rotgp_obs* out) {
   a.result = c->d_obs();
   cudaError_t e;
   {
-    // about reduce_blocks() blocks, each over whole x rows
-    const long long nrows = (long long)c->ny * c->nz;
+    // work items of 32 x 8 columns and a z range: split z until there are
+    // about reduce_blocks() items (at least 16 planes each), at most that
+    // many blocks (the partials buffer), items taken grid-stride
+    const long long tiles = (long long)((c->nx + 31) / 32) * ((c->ny + 7) / 8);
     const long long want = reduce_blocks(c, c->sites);
-    a.rows_per_block = (int)((nrows + want - 1) / want);
-    const int blocks = (int)((nrows + a.rows_per_block - 1) / a.rows_per_block);
+    const int nz = c->grid.dim == 3 ? c->nz : 1;
+    const long long zparts =
+        std::max(1LL, std::min<long long>((want + tiles - 1) / tiles, nz / 16));
+    a.zchunk = (int)((nz + zparts - 1) / zparts);
+    const long long items = tiles * ((nz + a.zchunk - 1) / a.zchunk);
+    const int blocks = (int)std::min(items, want);
     Timed t(c, K_OBS);
     e = launch_observables(c->fp64, a, blocks, 256, c->stream);
   }

@@ -180,7 +180,9 @@ int rotgp_info(const rotgp_ctx* ctx, rotgp_solver_info* out);
  * C >= the halo H of rotgp_info; complex float takes 8 or 16 with 2 lines
  * per thread, and 8 or 16 (TMA forms, even N_x) or 16 or 64 with one;
  * double takes 16 or 64), ring slots (3 or 4; 5 or 6 too in the TMA forms
- * with one line per thread and chunk 8), warps per block (1..8) and
+ * with one line per thread and chunk 8), warps per block (1..8; the TMA
+ * forms size their own blocks: one wave of persistent warps, up to 16 per
+ * block, taking 32-line units round-robin) and
  * segments each line is split into (clamped to the number of chunks).
  * The one-line-per-thread TMA forms (chunk 8 or 16) solve the unfolded
  * system psi' = 2 A^-1 psi - psi and serve imaginary-time steps; real-time

@@ -103,8 +103,12 @@ __device__ void combine_all(const double* partials, double* fin) {
 // Work items (tile, z range) are taken grid-stride.
 constexpr int kObsTX = 32, kObsTY = 8;
 
+// fused multiply-add in the working precision
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
 template <class T>
-__global__ void __launch_bounds__(256) k_observables(const obs_args a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_observables(const obs_args a) {
   using C = cpx<T>;
   constexpr int TX = kObsTX, TY = kObsTY, WX = TX + 4, WY = TY + 4;
   __shared__ C tile[2][WY][WX];
@@ -124,6 +128,7 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
   const T hz = a.dim == 3 ? (T)a.hz : (T)0;
   const T hgam2 = (T)a.hgam2, hnu2 = (T)a.hnu2, hlam2 = (T)a.hlam2;
   const bool d3 = a.dim == 3;
+  const T l0 = (T)2 * (ihx2 + ihy2 + ihz2), l04 = (T)30 * (c12x + c12y + c12z);
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int tiles_x = (nx + TX - 1) / TX, tiles_y = (ny + TY - 1) / TY;
   const int zlen = a.zchunk, zparts = (nz + zlen - 1) / zlen;
@@ -148,6 +153,8 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
     const T x = x0 + (T)i * hx;
     const T y = y0 + (T)j * hy;
     const T xxv = hgam2 * x * x + hnu2 * y * y;
+    const T x2 = x * x, y2 = y * y;
+    const T yh = y * i2hx, xh = x * i2hy, y12 = y * i12hx, x12 = x * i12hy;
     T kf = (T)k0;  // the plane index as a number, advanced per plane
     // the column's window z-2 .. z+2
     C w[5];
@@ -174,6 +181,8 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
       __syncthreads();
       const bool interior = i >= 1 && i < nx && j >= 1 && j < ny && (!d3 || k >= 1);
       if (interior) {
+        // the same terms with the sums and differences of each axis formed
+        // once (in 2D the z points are zero and ihz2 = 0)
         const C c = w[2];
         const C xp = tile[buf][ty + 2][tx + 3], xm = tile[buf][ty + 2][tx + 1];
         const C xp2 = tile[buf][ty + 2][tx + 4], xm2 = tile[buf][ty + 2][tx];
@@ -182,36 +191,41 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
         const C zp = w[3], zm = w[1], zp2 = w[4], zm2 = w[0];
         const T z = z0 + kf * hz;
         const T V = xxv + hlam2 * z * z;
-        C lap = ihx2 * (xp + xm - (T)2 * c) + ihy2 * (yp + ym - (T)2 * c);
-        if (d3) lap = lap + ihz2 * (zp + zm - (T)2 * c);
-        const C dx = i2hx * (xp - xm), dy = i2hy * (yp - ym);
-        const T re = c.x, im = c.y, dens = re * re + im * im;
-        const T hr = (T)-0.5 * lap.x + V * re + om * (y * dx.y - x * dy.y);
-        const T hi = (T)-0.5 * lap.y + V * im + om * (-(y * dx.x) + x * dy.x);
-        // -Omega L_z psi = -Omega i (y D_x - x D_y) psi
-        const C lz = y * dx - x * dy;  // L_z psi / i
-        const C hlin = mk<T>((T)-0.5 * lap.x + V * c.x + om * lz.y,
-                             (T)-0.5 * lap.y + V * c.y - om * lz.x);
+        const C sx = xp + xm, sy = yp + ym, sz = zp + zm;    // neighbour sums
+        const C ex = xp2 + xm2, ey = yp2 + ym2, ez = zp2 + zm2;
+        const C dx = xp - xm, dy = yp - ym;                  // central differences
+        const C fx = xp2 - xm2, fy = yp2 - ym2;
+        const T re = c.x, im = c.y, dens = fmat(re, re, im * im);
+        // -lap/2 + V and the rotation term, 3-point and 5-point forms;
+        // L_z psi / i = y D_x psi - x D_y psi
+        const T lapr = fmat(ihx2, sx.x, fmat(ihy2, sy.x, fmat(ihz2, sz.x, -l0 * re)));
+        const T lapi = fmat(ihx2, sx.y, fmat(ihy2, sy.y, fmat(ihz2, sz.y, -l0 * im)));
+        const T lzr = fmat(yh, dx.x, -xh * dy.x), lzi = fmat(yh, dx.y, -xh * dy.y);
+        const T hr = fmat((T)-0.5, lapr, fmat(V, re, om * lzi));
+        const T hi = fmat((T)-0.5, lapi, fmat(V, im, -om * lzr));
+        const T l4r = fmat(c12x, fmat((T)16, sx.x, -ex.x),
+                           fmat(c12y, fmat((T)16, sy.x, -ey.x),
+                                fmat(c12z, fmat((T)16, sz.x, -ez.x), -l04 * re)));
+        const T l4i = fmat(c12x, fmat((T)16, sx.y, -ex.y),
+                           fmat(c12y, fmat((T)16, sy.y, -ey.y),
+                                fmat(c12z, fmat((T)16, sz.y, -ez.y), -l04 * im)));
+        const T z4r = fmat(y12, fmat((T)8, dx.x, -fx.x), -x12 * fmat((T)8, dy.x, -fy.x));
+        const T z4i = fmat(y12, fmat((T)8, dx.y, -fx.y), -x12 * fmat((T)8, dy.y, -fy.y));
+        const T h4r = fmat((T)-0.5, l4r, fmat(V, re, om * z4i));
+        const T h4i = fmat((T)-0.5, l4i, fmat(V, im, -om * z4r));
+        const T gd = g * dens;
         t[0] += dens;
-        t[1] += re * re;
-        t[2] += im * im;
-        t[3] += re * hr;
-        t[4] += g * dens * re * re;
-        t[5] += im * hi;
-        t[6] += g * dens * im * im;
-        t[7] += re * hlin.x + im * hlin.y;
-        t[8] += g * dens * dens;
-        t[9] += x * x * dens;
-        t[10] += y * y * dens;
-        t[11] += z * z * dens;
-        C lap4 = c12x * ((T)16 * (xp + xm) - xp2 - xm2 - (T)30 * c) +
-                 c12y * ((T)16 * (yp + ym) - yp2 - ym2 - (T)30 * c);
-        if (d3) lap4 = lap4 + c12z * ((T)16 * (zp + zm) - zp2 - zm2 - (T)30 * c);
-        const C dx4 = i12hx * ((T)8 * (xp - xm) - xp2 + xm2);
-        const C dy4 = i12hy * ((T)8 * (yp - ym) - yp2 + ym2);
-        const C lz4 = y * dx4 - x * dy4;
-        t[12] += re * ((T)-0.5 * lap4.x + V * c.x + om * lz4.y) +
-                 im * ((T)-0.5 * lap4.y + V * c.y - om * lz4.x);
+        t[1] = fmat(re, re, t[1]);
+        t[2] = fmat(im, im, t[2]);
+        t[3] = fmat(re, hr, t[3]);
+        t[4] = fmat(gd * re, re, t[4]);
+        t[5] = fmat(im, hi, t[5]);
+        t[6] = fmat(gd * im, im, t[6]);
+        t[8] = fmat(gd, dens, t[8]);
+        t[9] = fmat(x2, dens, t[9]);
+        t[10] = fmat(y2, dens, t[10]);
+        t[11] = fmat(z * z, dens, t[11]);
+        t[12] = fmat(re, h4r, fmat(im, h4i, t[12]));
         t[13] = t[13] > dens ? t[13] : dens;
       }
 #pragma unroll
@@ -224,6 +238,8 @@ __global__ void __launch_bounds__(256) k_observables(const obs_args a) {
     }
     __syncthreads();  // the next item restages both buffers
   }
+  // q7, the complex-form energy density, is q3 + q5 site by site
+  t[7] = t[3] + t[5];
   double q[NQ];
 #pragma unroll
   for (int v = 0; v < NQ; ++v) q[v] = (double)t[v];

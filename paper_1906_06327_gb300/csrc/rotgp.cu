@@ -353,13 +353,6 @@ void lean_defaults(rotgp_ctx* c) {
     AxisPlan& ap = c->axis[a];
     if (!(a == 0 ? c->xmaps_ok && c->x_tma : c->smaps_ok)) continue;
     const AxisPlan keep = ap;
-    if (ap.sh.V != 1) {
-      ap.rt.set = true;
-      ap.rt.nseg = ap.nseg;
-      ap.rt.seg_chunks = ap.seg_chunks;
-      ap.rt.warm = ap.warm;
-      ap.rt.sh = ap.sh;
-    }
     const long long groups = (ap.lines + 31) / 32, nch = (ap.len + 7) / 8;
     const long long nseg = std::max<long long>(
         1, std::min<long long>(nch, (14LL * c->sm_count + groups / 2) / groups));
@@ -394,6 +387,13 @@ int plan_axes(rotgp_ctx* c) {
     const long long groups = (ap.lines + 32 * V - 1) / (32 * V);
     int rc = set_shape(c, a, V, C, R, 1, std::max<long long>(1, target / groups));
     if (rc) return rc == ROTGP_EINVAL ? fail(c, ROTGP_EUNSUPPORTED, "%s", c->err.c_str()) : rc;
+    // this folded plan also serves real-time steps whenever a one-line-per-
+    // lane TMA (unfolded) shape is chosen for the axis later
+    ap.rt.set = true;
+    ap.rt.nseg = ap.nseg;
+    ap.rt.seg_chunks = ap.seg_chunks;
+    ap.rt.warm = ap.warm;
+    ap.rt.sh = ap.sh;
     // banded-inverse stencil: complex float, even N_x (TMA rows of 16-byte
     // multiples; the separate x-stencil kernel also wants N_x % 4 == 0)
     int K = 0, B = 0;

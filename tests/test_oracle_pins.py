@@ -322,6 +322,27 @@ def test_energy_forms_agree_with_dense_rayleigh_quotient():
     assert abs(ob_rot["energy"] - rq_r) < 1e-12
 
 
+def test_real_part_mu_equals_complex_mu_on_a_stationary_state():
+    """On a stationary state the real-part equation (Eqs. e2dr/e3dr: the real
+    part of mu psi = H psi, with the rotation coupling Omega (y D_x - x D_y)
+    psi_I and the nonlinear g |psi|^2 psi_R) and the complex Rayleigh
+    quotient give the same mu.  The imaginary-time fixed point of the split
+    step (H1, x, y: a first-order splitting, Sec. 2) is stationary up to
+    O(Delta), so the two forms must approach each other linearly in Delta on
+    a rotating, interacting, anisotropic vortex state."""
+    N, h = (24, 24), (0.35, 0.35)
+    grid = Grid(N, h)
+    diffs = []
+    for dt in (4e-3, 2e-3):
+        phys = Phys(gamma=1.0, nu=1.2, g=15.0, omega=0.5, dt=dt)
+        psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(*N, 3))
+        psi, _ = oracle.steps(grid, phys, psi, int(40 / dt), True)
+        ob = oracle.observables(grid, phys, psi)
+        diffs.append(abs(ob["mu"] - ob["mu_c"]))
+    assert diffs[0] < 1e-4 * 2.65
+    assert 1.7 < diffs[0] / diffs[1] < 2.3, diffs
+
+
 def test_nonlinear_energy_term_closed_form():
     """The g terms of E_c and mu_c are g/2 and g times h^d sum |psi|^4 (unit norm)."""
     N, h = (16, 16), (0.4, 0.4)

@@ -23,6 +23,13 @@
 // per warp with cp.async; a chunk copy also brings the first point of the
 // next chunk (the stencil's right neighbour), so a chunk can be solved as
 // soon as its own copy lands while up to R-1 later chunks are in flight.
+//
+// The one-line-per-lane TMA forms of complex float (k_sweep_x1t,
+// k_sweep_s1t) use the same chunking with the unfolded solve of the same
+// system (A y = psi, psi' = 2y - psi: weights m2, al, be, no neighbour
+// points), TMA box loads and stores through R + 1 slots per warp, persistent
+// warps and programmatic launch; they serve imaginary time, while real time
+// keeps the folded form above (it holds the CN map's norm to rounding).
 #pragma once
 
 #include "common.cuh"

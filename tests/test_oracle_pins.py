@@ -370,6 +370,25 @@ def test_rms_of_gaussian():
     assert abs(ob["energy_c"] - (g1 + n1) / 2) < 5e-3
 
 
+def test_rms_of_gaussian_3d():
+    """The 3D anisotropic Gaussian exp(-(g x^2 + n y^2 + l z^2)/2) has
+    <x^2> = 1/(2 g) and so on (rms of Sec. 2); its energy is (g + n + l)/2."""
+    N, h = (40, 36, 44), (0.3, 0.3, 0.25)
+    grid = Grid(N, h)
+    x = grid.coords(0)[None, None, :]
+    y = grid.coords(1)[None, :, None]
+    z = grid.coords(2)[:, None, None]
+    g1, n1, l1 = 1.0, 1.4, 0.8
+    psi = np.exp(-(g1 * x ** 2 + n1 * y ** 2 + l1 * z ** 2) / 2).astype(np.complex128)
+    psi[0, :, :] = psi[:, 0, :] = psi[:, :, 0] = 0
+    ob = oracle.observables(grid, Phys(gamma=g1, nu=n1, lam=l1), psi)
+    assert abs(ob["rms_x"] - np.sqrt(0.5 / g1)) < 1e-8
+    assert abs(ob["rms_y"] - np.sqrt(0.5 / n1)) < 1e-8
+    assert abs(ob["rms_z"] - np.sqrt(0.5 / l1)) < 1e-8
+    assert abs(ob["rms_r"] - np.sqrt(0.5 / g1 + 0.5 / n1 + 0.5 / l1)) < 1e-8
+    assert abs(ob["energy_c"] - (g1 + n1 + l1) / 2) < 1.5e-2  # O(h^2): -9.5e-3 here
+
+
 @pytest.mark.parametrize("function,d", [(1, 1.0), (0, 1.0), (1, 1.3)])
 def test_initial_state_normalisation(function, d):
     """Eq. fun: the Gaussian has unit norm, the one-vortex state norm d_xy^2."""

@@ -372,7 +372,8 @@ def test_rms_of_gaussian():
 
 def test_rms_of_gaussian_3d():
     """The 3D anisotropic Gaussian exp(-(g x^2 + n y^2 + l z^2)/2) has
-    <x^2> = 1/(2 g) and so on (rms of Sec. 2); its energy is (g + n + l)/2."""
+    <x^2> = 1/(2 g) and so on (rms of Sec. 2); its energy is (g + n + l)/2,
+    reached at O(h^2) by the 3-point form and O(h^4) by the fourth-order one."""
     N, h = (40, 36, 44), (0.3, 0.3, 0.25)
     grid = Grid(N, h)
     x = grid.coords(0)[None, None, :]
@@ -387,6 +388,17 @@ def test_rms_of_gaussian_3d():
     assert abs(ob["rms_z"] - np.sqrt(0.5 / l1)) < 1e-8
     assert abs(ob["rms_r"] - np.sqrt(0.5 / g1 + 0.5 / n1 + 0.5 / l1)) < 1e-8
     assert abs(ob["energy_c"] - (g1 + n1 + l1) / 2) < 1.5e-2  # O(h^2): -9.5e-3 here
+    assert ob["max_density"] == 1.0  # the centre is a grid point
+    # the fourth-order form converges at O(h^4): ratio ~16 per halving of h
+    e1 = ob["energy4"] - (g1 + n1 + l1) / 2
+    grid2 = Grid(tuple(2 * n for n in N), tuple(v / 2 for v in h))
+    x = grid2.coords(0)[None, None, :]
+    y = grid2.coords(1)[None, :, None]
+    z = grid2.coords(2)[:, None, None]
+    psi2 = np.exp(-(g1 * x ** 2 + n1 * y ** 2 + l1 * z ** 2) / 2).astype(np.complex128)
+    psi2[0, :, :] = psi2[:, 0, :] = psi2[:, :, 0] = 0
+    e2 = oracle.observables(grid2, Phys(gamma=g1, nu=n1, lam=l1), psi2)["energy4"] - (g1 + n1 + l1) / 2
+    assert abs(e1) < 1e-3 and 12 < e1 / e2 < 20, (e1, e2)
 
 
 @pytest.mark.parametrize("function,d", [(1, 1.0), (0, 1.0), (1, 1.3)])

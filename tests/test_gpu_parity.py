@@ -410,6 +410,27 @@ def test_thomas_x_launch_shapes_fp32(shape, n, h, imag):
     assert np.max(np.abs(s.get_psi() - ref)) <= 5e-6 * np.max(np.abs(ref))
 
 
+def test_tma_sweeps_with_several_units_per_warp():
+    """Launch shapes whose 32-line units (4096 per sweep) outnumber the
+    resident persistent warps, so that every warp solves units in turn with
+    its ring's barrier phases and pending stores carried from one unit to
+    the next, match the oracle after two imaginary-time steps."""
+    n, h = (128, 128, 64), (0.12, 0.12, 0.14)
+    phys = dict(gamma=1.0, nu=1.1, lam=1.3, g=120.0, omega=0.7, dt=1e-3)
+    s = Solver(n, h, precision="fp32", **phys)
+    s.tune(0, 1, 8, 5, 1, 16)
+    s.tune(1, 1, 8, 5, 1, 16)
+    s.tune(2, 1, 8, 5, 1, 8)
+    info = s.info()
+    assert info["segments"] == [16, 16, 8] and info["lines_per_lane"] == [1, 1, 1]
+    R_ = inputs.random_phase_field(n[0], n[1], 7)
+    s.init_analytic(1, R_, 1.0, 1.0)
+    s.step_imag(2)
+    grid = Grid(n, h)
+    ref, _ = oracle.steps(grid, Phys(**phys), oracle.init_analytic(grid, 1, R_), 2, True)
+    assert np.max(np.abs(s.get_psi() - ref)) <= 5e-6 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("shape", [(1, 8, 3, 2), (1, 16, 4, 3), (2, 8, 3, 2), (1, 8, 4, 1),
                                    (1, 8, 5, 3), (1, 8, 6, 1)])
 @pytest.mark.parametrize("n,h", [((100, 66), (0.12, 0.15)), ((46, 36, 30), (0.3, 0.3, 0.25))])

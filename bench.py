@@ -43,6 +43,8 @@ def _args():
     p.add_argument("--skip-baselines", action="store_true",
                    help="no e2e and no CPU baseline (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--skip-large", action="store_true",
+                   help="no second roofline entry on the larger-than-L2 3D state")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
                    help="keep the default solver forms instead of timing the candidates")
     p.add_argument("--plan", default="",
@@ -66,18 +68,27 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu capture, if the kernel
-    source is unchanged since the capture; else None."""
+def _plan_str(info: dict, forms) -> str:
+    """Solver form and launch shape per axis (form:lines per lane,chunk,ring,segments)."""
+    return "/".join(f"{f}:{info['lines_per_lane'][ax]},{info['chunk'][ax]},"
+                    f"{info['ring'][ax]},{info['segments'][ax]}" for ax, f in enumerate(forms))
+
+
+def _traffic(kernel: str, workload: str, plan: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    capture, if it was taken with the same launch plan and the kernel sources
+    are unchanged since; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        rec = d["kernels"][kernel]
-        src = os.path.join(ROOT, "paper_1906_06327_gb300", "csrc", rec["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if h != rec["source_sha256"]:
+        rec = d["kernels"][f"{kernel}@{workload}"]
+        if rec["plan"] != plan:
             return None
+        for src_name, sha in rec["sources"].items():
+            src = os.path.join(ROOT, "paper_1906_06327_gb300", "csrc", src_name)
+            if hashlib.sha256(open(src, "rb").read()).hexdigest() != sha:
+                return None
         return float(rec["dram_bytes_per_launch"])
     except Exception:
         return None
@@ -157,22 +168,97 @@ def _workload(name):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def _cpu_oracle_rate(w, seconds_budget: float, max_steps: int | None = None):
-    """Time the FP64 oracle (one thread) on split steps of the same workload."""
+def _cpu_model() -> str:
+    """The host CPU's model name (x86 'model name', else lscpu's 'Model name')."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _oracle_worker(args):
+    """One oracle replica: FP64 split steps of the workload for about
+    ``seconds`` (at least one); returns (steps, seconds)."""
+    name, seconds, max_steps, seed_offset = args
     import oracle
     from paper_1906_06327_gb300 import inputs
+    w = inputs.WORKLOADS[name]
     grid = oracle.Grid(w.n, w.h)
     phys = oracle.Phys(gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt)
-    psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(w.n[0], w.n[1], w.seed))
+    psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(w.n[0], w.n[1],
+                                                                  w.seed + seed_offset))
     steps, total = 0, 0.0
     while True:
         t0 = time.perf_counter()
         psi, _ = oracle.steps(grid, phys, psi, 1, True)
         total += time.perf_counter() - t0
         steps += 1
-        if total >= seconds_budget or (max_steps and steps >= max_steps):
+        if total >= seconds or (max_steps and steps >= max_steps):
             break
+    return steps, total
+
+
+_REPLICA = {}
+
+
+def _replica_init(name: str):
+    """Pool initialiser: this worker's own seeded instance of the workload."""
+    import oracle
+    from paper_1906_06327_gb300 import inputs
+    w = inputs.WORKLOADS[name]
+    grid = oracle.Grid(w.n, w.h)
+    phys = oracle.Phys(gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt)
+    seed = w.seed + 1 + os.getpid() % 1000
+    _REPLICA.update(grid=grid, phys=phys, psi=oracle.init_analytic(
+        grid, 1, inputs.random_phase_field(w.n[0], w.n[1], seed)))
+
+
+def _replica_step(_):
+    """One FP64 imaginary-time split step of this worker's instance."""
+    import oracle
+    _REPLICA["psi"], _ = oracle.steps(_REPLICA["grid"], _REPLICA["phys"], _REPLICA["psi"], 1, True)
+    return 1
+
+
+def _oracle_pool(workers: int, name: str | None = None):
+    """A process pool of oracle replicas (spawned, so no worker inherits a CUDA
+    context); with ``name`` every worker holds its own instance of that workload."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    if name is None:
+        return ctx.Pool(workers)
+    return ctx.Pool(workers, initializer=_replica_init, initargs=(name,))
+
+
+def _cpu_oracle_rate(w, seconds_budget: float, max_steps: int | None = None):
+    """Time the FP64 oracle (one thread) on split steps of the same workload."""
+    steps, total = _oracle_worker((w.name, seconds_budget, max_steps, 0))
     return w.sites * steps / total, steps, total
+
+
+def _cpu_oracle_rate_all_cores(w, seconds_budget: float, workers: int):
+    """The oracle on every host core: one single-threaded replica per core,
+    each on its own seeded instance of the workload (the oracle itself is
+    unchanged); rate = all replicas' site-updates / the slowest replica's time."""
+    import oracle
+    oracle.build()
+    with _oracle_pool(workers) as pool:
+        res = pool.map(_oracle_worker, [(w.name, seconds_budget, None, k + 1)
+                                        for k in range(workers)])
+    steps = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return w.sites * steps / secs, steps, secs
 
 
 def run_reference(a, w):
@@ -181,27 +267,30 @@ def run_reference(a, w):
         return 0
     import oracle
     oracle.build()
-    from paper_1906_06327_gb300 import inputs
-    grid = oracle.Grid(w.n, w.h)
-    phys = oracle.Phys(gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt)
-    psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(w.n[0], w.n[1], w.seed))
-    for _ in range(a.warmup):
-        psi, _ = oracle.steps(grid, phys, psi, 1, True)
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        psi, _ = oracle.steps(grid, phys, psi, 1, True)
-    dt = time.perf_counter() - t0
-    value = w.sites * a.steps / dt
+    cores = os.cpu_count() or 1
+    # every bench step: one split step on each of `cores` replicas (each worker
+    # of the pool holds its own seeded instance, built before the clock starts)
+    with _oracle_pool(cores, w.name) as pool:
+        for _ in range(a.warmup):
+            pool.map(_replica_step, range(cores), chunksize=1)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            pool.map(_replica_step, range(cores), chunksize=1)
+        dt = time.perf_counter() - t0
+    value = w.sites * cores * a.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.n), "spacing": list(w.h),
-                   "step": "1 imaginary-time split step per bench step (bounded sample)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{a.steps} imaginary-time split steps of the {w.name} grid, "
-                                   "FP64 C oracle, 1 thread"},
+                   "step": f"{cores} imaginary-time split steps per bench step, spread over "
+                           f"{cores} single-threaded oracle replicas (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu": _cpu_model(),
+                         "sample": f"{a.steps} bench steps x {cores} replicas x 1 imaginary-"
+                                   f"time split step of the {w.name} grid, FP64 C oracle, one "
+                                   "thread per replica"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -209,6 +298,66 @@ def run_reference(a, w):
 
 
 # ------------------------------------------------------------------ GPU path
+def _roofline(kstats: dict, peak: float, peak_kind: str, workload: str, plan: str) -> dict:
+    """Roofline entry of the dominant kernel: algorithmic bytes per launch over
+    its mean CUDA-event duration, against the measured HBM copy bandwidth."""
+    dname, drec = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
+    avg_ms = drec["total_ms"] / drec["launches"]
+    achieved = drec["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    tot = max(1e-9, sum(x["total_ms"] for x in kstats.values()))
+    return {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dname, workload, plan),
+            "peak_source": peak_kind, "workload": workload, "plan": plan,
+            "algorithmic_bytes_per_launch": drec["bytes_per_launch"],
+            "avg_launch_ms": avg_ms,
+            "kernel_shares": {k: round(v["total_ms"] / tot, 4) for k, v in kstats.items()}}
+
+
+def _large_state_roofline(a, stream, flush, peak, peak_kind, name="3d-512x512x128-fp32",
+                          inner=50, reps=3):
+    """Throughput and dominant-kernel roofline on the 3D 512 x 512 x 128
+    complex-float state (268 MB per buffer, twice the L2), so that each sweep
+    streams its state from HBM.  Autotuned like the main workload; `reps`
+    blocks of `inner` imaginary-time split steps, each after an L2 flush."""
+    import torch
+    from paper_1906_06327_gb300 import inputs
+    from paper_1906_06327_gb300.rotgp import Solver
+    w = inputs.WORKLOADS[name]
+    s = Solver(w.n, w.h, gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt,
+               precision="fp32", stream=stream.cuda_stream)
+    s.init_analytic(1, seed=w.seed)
+    tuned = s.autotune(steps=5) if a.autotune else {"forms": ["thomas"] * 3}
+    plan = _plan_str(s.info(), tuned["forms"])
+    s.step_imag(inner)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        s.step_imag(inner)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    s.profile(True)
+    for _ in range(reps):
+        flush.zero_()
+        s.step_imag(inner)
+    torch.cuda.synchronize()
+    s.profile(False)
+    kstats = s.profile_read()
+    clk = clocks.stop()
+    s.close()
+    out = _roofline(kstats, peak, peak_kind, name, plan)
+    out["site_updates_per_s"] = w.sites * inner * reps / (ms * 1e-3)
+    out["split_steps"] = inner * reps
+    out["l2"] = "state 2 x 268 MB (twice the 129 MB L2); L2 flushed before every block"
+    out["clocks"] = clk
+    return out
+
+
 def run_ours(a, w):
     import numpy as np
     import torch
@@ -226,8 +375,7 @@ def run_ours(a, w):
     precision = w.precision
     s = Solver(w.n, w.h, gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt,
                precision=precision, stream=stream.cuda_stream)
-    R = inputs.random_phase_field(w.n[0], w.n[1], w.seed + rank)
-    s.init_analytic(1, R, 1.0, 1.0)
+    s.init_analytic(1, None, 1.0, 1.0, seed=w.seed + rank)
     # solver forms picked by timing them on this grid (untimed setup, like a plan)
     if a.plan:
         # form and launch shape per axis: form:V,C,R,segments separated by "/"
@@ -308,18 +456,13 @@ def run_ours(a, w):
 
     # roofline of the dominant kernel (largest share of the timed region)
     peak, peak_kind = _peaks()
-    dom = max(kstats.items(), key=lambda kv: kv[1]["total_ms"])
-    dname, drec = dom
-    avg_ms = drec["total_ms"] / drec["launches"]
-    achieved = drec["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
     launches = sum(v["launches"] for v in kstats.values())
-    roofline = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dname),
-                "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": drec["bytes_per_launch"],
-                "avg_launch_ms": avg_ms,
-                "kernel_shares": {k: round(v["total_ms"] / max(1e-9, sum(
-                    x["total_ms"] for x in kstats.values())), 4) for k, v in kstats.items()}}
+    plan = _plan_str(s.info(), tuned["forms"])
+    roofline = _roofline(kstats, peak, peak_kind, w.name, plan)
+    # the same on a state twice the size of L2 (HBM-bound by construction)
+    roofline_hbm = None
+    if not a.skip_large and world == 1:
+        roofline_hbm = _large_state_roofline(a, stream, flush, peak, peak_kind)
 
     e2e = None
     cpu = None
@@ -346,10 +489,16 @@ def run_ours(a, w):
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 10 * 8 + 4,
                "steps": a.e2e_steps, "api": "rotgp_set_psi + rotgp_step_imag + "
                                             "rotgp_observables + rotgp_get_psi, pinned host"}
-        rate, nsteps, secs = _cpu_oracle_rate(w, a.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nsteps} imaginary-time split step(s) of the {w.name} grid "
-                         f"({secs:.1f} s), FP64 C oracle, 1 thread"}
+        cores = os.cpu_count() or 1
+        rate, nsteps, secs = _cpu_oracle_rate_all_cores(w, a.cpu_seconds, cores)
+        rate1, nsteps1, secs1 = _cpu_oracle_rate(w, a.cpu_seconds / 2)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "cpu": _cpu_model(),
+               "sample": f"{nsteps} imaginary-time split steps of the {w.name} grid over "
+                         f"{cores} single-threaded FP64 C oracle replicas (one per core, "
+                         f"{secs:.1f} s)",
+               "one_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"{nsteps1} split step(s), {secs1:.1f} s"}}
 
     info = s.info()
     if rank == 0:
@@ -370,13 +519,11 @@ def run_ours(a, w):
                              "state can stay L2-resident within a step",
                        "parallelism": f"replicas x{world}",
                        "solver_forms": tuned["forms"],
-                       "plan": "/".join(
-                           f"{f}:{info['lines_per_lane'][ax]},{info['chunk'][ax]},"
-                           f"{info['ring'][ax]},{info['segments'][ax]}"
-                           for ax, f in enumerate(tuned["forms"])),
+                       "plan": plan,
                        "solver": info},
             "gpu_launches": launches,
             "roofline": roofline,
+            "roofline_hbm": roofline_hbm,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

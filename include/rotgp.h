@@ -146,16 +146,34 @@ int rotgp_set_omega(rotgp_ctx* ctx, double omega);
 /* Initial state of Eq. fun, normalised to unit norm:
  *   psi = (x + i y)/sqrt(pi d_xy^2) exp(-(x^2+y^2)/(2 d_xy^2) + 2 pi i R)
  *   [* (pi d_z^2)^(-1/4) exp(-z^2/(2 d_z^2)) in 3D]
- * function = 1 (one vortex) or 0 (Gaussian: x + i y -> 1).  phase_R: host
- * array of (N_x+1)(N_y+1) doubles in [0,1) (x fastest), the random numbers
- * R(x, y); NULL for no random phase. */
-int rotgp_init_analytic(rotgp_ctx* ctx, int function, const double* phase_R,
+ * function = 1 (one vortex) or 0 (Gaussian: x + i y -> 1).  With
+ * random_phase != 0, R(x_i, y_j) in [0,1) is drawn on the device from the
+ * counter-based SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014):
+ * number n = j (N_x + 1) + i of the stream seeded with `seed`, i.e. the
+ * state seed + (n + 1) 0x9E3779B97F4A7C15 through the generator's output
+ * mix, top 53 bits scaled by 2^-53.  The same R depends on (i, j) only and
+ * is shared by every z plane.  random_phase = 0 leaves the phase out (R = 0).
+ * The state is fully determined by (grid, function, seed, d_xy, d_z), so a
+ * C caller reproduces a seeded start without any host-side generator.
+ * ROTGP_EINVAL for another function value or a width <= 0. */
+int rotgp_init_analytic(rotgp_ctx* ctx, int function, int random_phase, unsigned long long seed,
                         double d_xy, double d_z);
 
+/* The same initial state with the random numbers R supplied by the caller:
+ * phase_R = host array of (N_x+1)(N_y+1) doubles in [0,1) (x fastest), read
+ * during the call; NULL for no random phase. */
+int rotgp_init_analytic_field(rotgp_ctx* ctx, int function, const double* phase_R, double d_xy,
+                              double d_z);
+
 /* Load a wave function of (N+1)^d points (see conventions) from host or
- * device memory, complex double (src_is_fp64 = 1) or complex float.  Values
- * are taken as they are (not renormalised); edge points are ignored. */
-int rotgp_set_psi(rotgp_ctx* ctx, const void* src, int src_on_device, int src_is_fp64);
+ * device memory, complex double (src_is_fp64 = 1) or complex float; edge
+ * points are ignored.  normalise = 1 renormalises the loaded state to unit
+ * norm (h_x h_y [h_z] sum |psi|^2 = 1, applied as the pending scale, as
+ * after an imaginary-time step); normalise = 0 keeps the values as they are
+ * (real-time runs from a given state).  Synchronises the stream; with
+ * normalise = 1 a zero or non-finite norm gives ROTGP_ENONFINITE. */
+int rotgp_set_psi(rotgp_ctx* ctx, const void* src, int src_on_device, int src_is_fp64,
+                  int normalise);
 
 /* Store the current wave function into (N+1)^d points of host or device
  * memory, complex double or float; synchronises the stream. */
@@ -265,7 +283,10 @@ int rotgp_profile_read(rotgp_ctx* ctx, rotgp_kstat* out, int max, int* count);
  * Scratch: a file-scope device array of about 448 KiB inside the library, which
  * every GPU that loads the library holds until exit.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture.  All
+ * the device current and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset reloads the
+ * library's device image, so calls after a device reset in the same process
+ * are not supported.  All
  * calls share the array: calls whose work overlaps on the GPU race and must
  * be ordered by the caller.  At most 33,554,432 grid points; larger grids
  * are rejected with ROTGP_EINVAL (message via rotgp_last_error(NULL)). */

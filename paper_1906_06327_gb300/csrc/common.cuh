@@ -253,8 +253,9 @@ cudaError_t launch_norm(bool fp64, const void* psi, long long nsites, double vol
                         double* norm_out, int* flags, int blocks, int threads, cudaStream_t s);
 cudaError_t launch_init_analytic(bool fp64, void* psi, int nx, int ny, int nz, int dim,
                                  double x0, double hx, double y0, double hy, double z0,
-                                 double hz, int function, const double* R, double d_xy,
-                                 double d_z, cudaStream_t s);
+                                 double hz, int function, int phase_mode, const double* R,
+                                 unsigned long long seed, double d_xy, double d_z,
+                                 cudaStream_t s);
 cudaError_t launch_pack(bool fp64_store, bool fp64_src, const void* src, void* psi, int nx,
                         int ny, int nz, int dim, double* scale, cudaStream_t s);
 cudaError_t launch_unpack(bool fp64_store, bool fp64_dst, const void* psi, void* dst, int nx,

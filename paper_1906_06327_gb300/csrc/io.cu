@@ -6,13 +6,31 @@
 
 namespace rotgp {
 
+// Random number n of the SplitMix64 stream seeded with `seed` (Steele, Lea
+// and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+// the counter state seed + (n + 1) * 0x9E3779B97F4A7C15 passed through the
+// generator's output mix (two xor-shift-multiply rounds and a final
+// xor-shift), all modulo 2^64; its top 53 bits scaled by 2^-53 give a double
+// in [0, 1).  Counter based, so every grid point draws its own number.
+__device__ __forceinline__ double splitmix64_unit(unsigned long long seed, unsigned long long n) {
+  unsigned long long z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
 // Eq. fun: psi = (x + i y)/sqrt(pi d^2) exp(-(x^2+y^2)/(2 d^2)) e^{2 pi i R}
 // [3D: * (pi d_z^2)^(-1/4) exp(-z^2/(2 d_z^2))]; function 0: (x + i y) -> 1.
-// Evaluated in double, stored in T; R indexed on the (N_x+1)(N_y+1) plane.
+// Evaluated in double, stored in T.  R(x_i, y_j) is the number of the point
+// n = j (N_x + 1) + i of the (N_x+1)(N_y+1) plane: read from the table R
+// (phase_mode 1) or drawn from SplitMix64(seed) (phase_mode 2); phase_mode 0
+// leaves the phase out.
 template <class T>
 __global__ void k_init_analytic(cpx<T>* psi, int nx, int ny, int nz, int dim, double x0,
                                 double hx, double y0, double hy, double z0, double hz,
-                                int function, const double* R, double d_xy, double d_z) {
+                                int function, int phase_mode, const double* R,
+                                unsigned long long seed, double d_xy, double d_z) {
   const long long n = (long long)nx * ny * nz;
   const double kPi = 3.14159265358979323846;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
@@ -34,7 +52,9 @@ __global__ void k_init_analytic(cpx<T>* psi, int nx, int ny, int nz, int dim, do
       amp *= pow(kPi * d_z * d_z, -0.25) * exp(-z * z / (2.0 * d_z * d_z));
     }
     double sn = 0.0, cs = 1.0;
-    if (R) sincos(2.0 * kPi * R[(size_t)j * (nx + 1) + i], &sn, &cs);
+    const unsigned long long pn = (unsigned long long)j * (nx + 1) + i;
+    if (phase_mode == 1) sincos(2.0 * kPi * R[pn], &sn, &cs);
+    if (phase_mode == 2) sincos(2.0 * kPi * splitmix64_unit(seed, pn), &sn, &cs);
     psi[idx] = mk<T>((T)(amp * (pr * cs - pi * sn)), (T)(amp * (pr * sn + pi * cs)));
   }
 }
@@ -90,17 +110,18 @@ static int grid_for(long long n, int threads) {
 
 cudaError_t launch_init_analytic(bool fp64, void* psi, int nx, int ny, int nz, int dim,
                                  double x0, double hx, double y0, double hy, double z0,
-                                 double hz, int function, const double* R, double d_xy,
-                                 double d_z, cudaStream_t s) {
+                                 double hz, int function, int phase_mode, const double* R,
+                                 unsigned long long seed, double d_xy, double d_z,
+                                 cudaStream_t s) {
   const int threads = 256, blocks = grid_for((long long)nx * ny * nz, threads);
   if (fp64)
     k_init_analytic<double><<<blocks, threads, 0, s>>>(static_cast<cpx<double>*>(psi), nx, ny,
                                                        nz, dim, x0, hx, y0, hy, z0, hz,
-                                                       function, R, d_xy, d_z);
+                                                       function, phase_mode, R, seed, d_xy, d_z);
   else
     k_init_analytic<float><<<blocks, threads, 0, s>>>(static_cast<cpx<float>*>(psi), nx, ny, nz,
-                                                      dim, x0, hx, y0, hy, z0, hz, function, R,
-                                                      d_xy, d_z);
+                                                      dim, x0, hx, y0, hy, z0, hz, function,
+                                                      phase_mode, R, seed, d_xy, d_z);
   return cudaGetLastError();
 }
 

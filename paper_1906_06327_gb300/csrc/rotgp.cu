@@ -862,6 +862,44 @@ void ctx_add_steps(rotgp_ctx* c, long long n) { c->steps += n; }
 void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
 }  // namespace rotgp
 
+namespace {
+
+// Eq. fun into the current buffer (phase_mode as k_init_analytic), then the
+// norm and the pending scale 1/sqrt(norm).
+int init_state(rotgp_ctx* c, int function, int phase_mode, const double* phase_R,
+               unsigned long long seed, double d_xy, double d_z) {
+  if (function != 0 && function != 1) return fail(c, ROTGP_EINVAL, "function must be 0 or 1");
+  if (!(d_xy > 0) || (c->grid.dim == 3 && !(d_z > 0)))
+    return fail(c, ROTGP_EINVAL, "widths must be positive");
+  cudaError_t e = cudaSuccess;
+  if (phase_mode == 1) {
+    e = cudaMemcpyAsync(c->dR, phase_R, (size_t)(c->nx + 1) * (c->ny + 1) * 8,
+                        cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy phase field");
+  }
+  {
+    Timed t(c, K_INIT);
+    e = launch_init_analytic(c->fp64, c->psi[c->cur], c->nx, c->ny, c->nz, c->grid.dim, c->x0,
+                             c->grid.h[0], c->y0, c->grid.h[1], c->z0,
+                             c->grid.dim == 3 ? c->grid.h[2] : 0.0, function, phase_mode,
+                             phase_mode == 1 ? c->dR : nullptr, seed, d_xy, d_z, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  if ((e = cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "reset flags");
+  {
+    Timed t(c, K_NORM);
+    e = launch_norm(c->fp64, c->psi[c->cur], c->sites, c->vol, 1, c->partials, c->counter,
+                    c->d_scale(), c->d_norm(), c->d_flags(), reduce_blocks(c, c->sites), 256,
+                    c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "norm kernel");
+  c->steps = 0;
+  return check_flags(c);  // also releases phase_R
+}
+
+}  // namespace
+
 // =============================================================== C ABI
 extern "C" {
 
@@ -1066,40 +1104,20 @@ int rotgp_set_omega(rotgp_ctx* c, double omega) {
   return rotgp_set_phys(c, &p);
 }
 
-int rotgp_init_analytic(rotgp_ctx* c, int function, const double* phase_R, double d_xy,
-                        double d_z) {
+int rotgp_init_analytic(rotgp_ctx* c, int function, int random_phase, unsigned long long seed,
+                        double d_xy, double d_z) {
   if (!c) return ROTGP_EINVAL;
-  if (function != 0 && function != 1) return fail(c, ROTGP_EINVAL, "function must be 0 or 1");
-  if (!(d_xy > 0) || (c->grid.dim == 3 && !(d_z > 0)))
-    return fail(c, ROTGP_EINVAL, "widths must be positive");
-  cudaError_t e = cudaSuccess;
-  if (phase_R) {
-    e = cudaMemcpyAsync(c->dR, phase_R, (size_t)(c->nx + 1) * (c->ny + 1) * 8,
-                        cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "copy phase field");
-  }
-  {
-    Timed t(c, K_INIT);
-    e = launch_init_analytic(c->fp64, c->psi[c->cur], c->nx, c->ny, c->nz, c->grid.dim, c->x0,
-                             c->grid.h[0], c->y0, c->grid.h[1], c->z0,
-                             c->grid.dim == 3 ? c->grid.h[2] : 0.0, function,
-                             phase_R ? c->dR : nullptr, d_xy, d_z, c->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
-  if ((e = cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream)) != cudaSuccess)
-    return cuda_fail(c, e, "reset flags");
-  {
-    Timed t(c, K_NORM);
-    e = launch_norm(c->fp64, c->psi[c->cur], c->sites, c->vol, 1, c->partials, c->counter,
-                    c->d_scale(), c->d_norm(), c->d_flags(), reduce_blocks(c, c->sites), 256,
-                    c->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(c, e, "norm kernel");
-  c->steps = 0;
-  return check_flags(c);  // also releases phase_R
+  return init_state(c, function, random_phase ? 2 : 0, nullptr, seed, d_xy, d_z);
 }
 
-int rotgp_set_psi(rotgp_ctx* c, const void* src, int src_on_device, int src_is_fp64) {
+int rotgp_init_analytic_field(rotgp_ctx* c, int function, const double* phase_R, double d_xy,
+                              double d_z) {
+  if (!c) return ROTGP_EINVAL;
+  return init_state(c, function, phase_R ? 1 : 0, phase_R, 0ull, d_xy, d_z);
+}
+
+int rotgp_set_psi(rotgp_ctx* c, const void* src, int src_on_device, int src_is_fp64,
+                  int normalise) {
   if (!c || !src) return c ? fail(c, ROTGP_EINVAL, "null source") : ROTGP_EINVAL;
   const size_t pts = c->staging_bytes / 16;
   const size_t bytes = pts * (src_is_fp64 ? 16 : 8);
@@ -1118,10 +1136,18 @@ int rotgp_set_psi(rotgp_ctx* c, const void* src, int src_on_device, int src_is_f
   if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
   if ((e = cudaMemsetAsync(c->iflags, 0, sizeof(int), c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "reset flags");
+  if (normalise) {
+    // the norm and the pending scale 1/sqrt(norm), as after an imaginary-time step
+    Timed t(c, K_NORM);
+    e = launch_norm(c->fp64, c->psi[c->cur], c->sites, c->vol, 1, c->partials, c->counter,
+                    c->d_scale(), c->d_norm(), c->d_flags(), reduce_blocks(c, c->sites), 256,
+                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "norm kernel");
+  }
   c->steps = 0;
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_psi");
-  return ROTGP_OK;
+  return normalise ? check_flags(c) : ROTGP_OK;
 }
 
 int rotgp_get_psi(rotgp_ctx* c, void* dst, int dst_on_device, int dst_is_fp64) {

@@ -37,6 +37,11 @@
 
 namespace rotgp {
 
+// Dynamic shared-memory opt-in of a kernel on the current device (sweep_s.cu):
+// `bytes`, or all the device allows beside the kernel's static shared memory.
+cudaError_t allow_smem_bytes(const void* fn, int bytes);
+cudaError_t allow_smem(const void* fn);
+
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
   unsigned s = (unsigned)__cvta_generic_to_shared(dst);

@@ -10,6 +10,7 @@
 // and the ring are described in sweep_common.cuh.
 #include <algorithm>
 #include <map>
+#include <set>
 #include <mutex>
 #include <tuple>
 
@@ -429,26 +430,43 @@ cudaError_t resident_grid(const void* fn, long long units, size_t smem_per_warp,
   return cudaSuccess;
 }
 
-cudaError_t allow_smem(const void* fn, bool* done) {
-  if (*done) return cudaSuccess;
-  int dev = 0, optin = 0;
-  cudaFuncAttributes fa{};
+// Opt a kernel in to `bytes` of dynamic shared memory (bytes < 0: all that
+// the device allows beside its static shared memory), once per kernel and
+// device: the attribute belongs to the kernel on the current device, so a
+// context on a second device in the same process sets its own.
+cudaError_t allow_smem_bytes(const void* fn, int bytes) {
+  int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
-  if (e == cudaSuccess) *done = true;
-  return e;
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;
+  const auto key = std::make_tuple(fn, dev, bytes);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return cudaSuccess;
+  }
+  if (bytes < 0) {
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    bytes = optin - (int)fa.sharedSizeBytes;
+  }
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  done.insert(key);
+  return cudaSuccess;
 }
+
+cudaError_t allow_smem(const void* fn) { return allow_smem_bytes(fn, -1); }
 
 template <class T, int V, int C>
 static cudaError_t dispatch_s(bool reduce, const stream_args& a, const sweep_shape& sh,
                               cudaStream_t s) {
-  static bool done[2] = {false, false};
   auto fn = reduce ? k_sweep_strided<T, V, C, true> : k_sweep_strided<T, V, C, false>;
-  cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
+  cudaError_t e = allow_smem((const void*)fn);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
   return cudaGetLastError();
@@ -457,11 +475,10 @@ static cudaError_t dispatch_s(bool reduce, const stream_args& a, const sweep_sha
 template <int C>
 static cudaError_t dispatch_s2(bool reduce, const stream_args& a, const sweep_shape& sh,
                                cudaStream_t s) {
-  static bool done[4] = {false, false, false, false};
   if (sh.R != 3 && sh.R != 4) return cudaErrorInvalidValue;
   auto fn = sh.R == 3 ? (reduce ? k_sweep_strided2<C, true, 3> : k_sweep_strided2<C, false, 3>)
                       : (reduce ? k_sweep_strided2<C, true, 4> : k_sweep_strided2<C, false, 4>);
-  cudaError_t e = allow_smem((const void*)fn, &done[(sh.R == 4 ? 2 : 0) + (reduce ? 1 : 0)]);
+  cudaError_t e = allow_smem((const void*)fn);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
   return cudaGetLastError();
@@ -707,11 +724,10 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_s1t(const __grid_c
 template <int C, int R, int AX>
 static cudaError_t dispatch_s1t(bool reduce, const stream_args& a, const sweep_shape& sh,
                                 const void* map, const void* omap, cudaStream_t s) {
-  static bool done[2] = {false, false};
   const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
   const CUtensorMap& om = *static_cast<const CUtensorMap*>(omap);
   auto fn = reduce ? k_sweep_s1t<C, true, R, AX> : k_sweep_s1t<C, false, R, AX>;
-  cudaError_t e = allow_smem((const void*)fn, &done[reduce ? 1 : 0]);
+  cudaError_t e = allow_smem((const void*)fn);
   if (e != cudaSuccess) return e;
   const long long units = (long long)((a.nx + 31) / 32) * (a.nlines / a.nx) * a.nseg;
   int W = 1;

@@ -15,7 +15,6 @@
 
 namespace rotgp {
 
-cudaError_t allow_smem(const void* fn, bool* done);
 
 template <class T, int V, int C, bool IMAG, bool VEC16>
 __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
@@ -746,11 +745,10 @@ size_t x1t_smem_per_warp(int C, int R) { return (size_t)(R + 1) * 32 * C * 8; }
 template <int C, int R>
 static cudaError_t dispatch_x1t(bool imag, const stream_args& a, const sweep_shape& sh,
                                 const void* map, const void* omap, cudaStream_t s) {
-  static bool done[2] = {false, false};
   const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
   const CUtensorMap& om = *static_cast<const CUtensorMap*>(omap);
   auto fn = imag ? k_sweep_x1t<C, true, R> : k_sweep_x1t<C, false, R>;
-  cudaError_t e = allow_smem((const void*)fn, &done[imag ? 1 : 0]);
+  cudaError_t e = allow_smem((const void*)fn);
   if (e != cudaSuccess) return e;
   const long long units = (a.nlines + 31) / 32 * a.nseg;
   int W = 1;
@@ -764,7 +762,6 @@ static cudaError_t dispatch_x1t(bool imag, const stream_args& a, const sweep_sha
 template <int C, int R>
 static cudaError_t dispatch_x2r(bool imag, bool vec16, const stream_args& a,
                                 const sweep_shape& sh, const void* map, cudaStream_t s) {
-  static bool done[6] = {false, false, false, false, false, false};
   const bool tma = map != nullptr && vec16 && sh.warps_per_block <= 4;
   static const CUtensorMap none{};
   const CUtensorMap& m = tma ? *static_cast<const CUtensorMap*>(map) : none;
@@ -774,7 +771,7 @@ static cudaError_t dispatch_x2r(bool imag, bool vec16, const stream_args& a,
                   : (imag ? k_sweep_x2<C, true, false, false, R>
                           : k_sweep_x2<C, false, false, false, R>);
   const int k = (tma ? 4 : vec16 ? 2 : 0) + (imag ? 1 : 0);
-  cudaError_t e = allow_smem((const void*)fn, &done[k]);
+  cudaError_t e = allow_smem((const void*)fn);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem + (tma ? 128 : 0), s>>>(m, a);
   return cudaGetLastError();
@@ -791,10 +788,9 @@ static cudaError_t dispatch_x2(bool imag, bool vec16, const stream_args& a, cons
 template <class T, int V, int C>
 static cudaError_t dispatch_x(bool imag, bool vec16, const stream_args& a, const sweep_shape& sh,
                               cudaStream_t s) {
-  static bool done[4] = {false, false, false, false};
   auto fn = vec16 ? (imag ? k_sweep_x<T, V, C, true, true> : k_sweep_x<T, V, C, false, true>)
                   : (imag ? k_sweep_x<T, V, C, true, false> : k_sweep_x<T, V, C, false, false>);
-  cudaError_t e = allow_smem((const void*)fn, &done[(vec16 ? 2 : 0) + (imag ? 1 : 0)]);
+  cudaError_t e = allow_smem((const void*)fn);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem, s>>>(a);
   return cudaGetLastError();

@@ -405,13 +405,10 @@ void xy_tile_geometry(int K, int* TX, int* TY, int* R, int* WX) {
   *WX = 64 + 2 * KP + 2;
 }
 
-// opt an instantiation in to its dynamic shared memory, once
+// opt an instantiation in to its dynamic shared memory, once per device
 template <int K, bool IMAG, bool REDUCE>
 cudaError_t xy_allow_smem() {
-  static const cudaError_t e = cudaFuncSetAttribute(
-      k_xy_pass<K, IMAG, REDUCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)xy_geom<K>::SMEM);
-  return e;
+  return allow_smem_bytes((const void*)k_xy_pass<K, IMAG, REDUCE>, (int)xy_geom<K>::SMEM);
 }
 
 template <int K, bool IMAG, bool REDUCE>
@@ -451,9 +448,7 @@ cudaError_t launch_xy_k(const CUtensorMap& m, const tile_args& a, unsigned block
 
 template <int K, bool IMAG>
 cudaError_t x_allow_smem() {
-  static const cudaError_t e = cudaFuncSetAttribute(
-      k_x_pass<K, IMAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x_geom<K>::SMEM);
-  return e;
+  return allow_smem_bytes((const void*)k_x_pass<K, IMAG>, (int)x_geom<K>::SMEM);
 }
 
 int x_pass_ctas_per_sm(int K) {

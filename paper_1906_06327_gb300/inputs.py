@@ -95,8 +95,13 @@ WL_3D_256_FP32 = Workload("3d-256x256x128-fp32", (256, 256, 128), (0.08, 0.08, 0
 WL_2D_4096_FP32 = Workload("2d-4096-fp32", (4096, 4096), (0.01, 0.01), 1.0, 1.05,
                            1.0, 1000.0, 0.9, 2.5e-4, 0)
 
+# A larger-than-L2 3D shape with the 256 x 256 x 128 physics: 512 x 512 x 128
+# (268 MB per complex-float state, twice the L2).
+WL_3D_512_FP32 = Workload("3d-512x512x128-fp32", (512, 512, 128), (0.08, 0.08, 0.1),
+                          1.0, 1.0, 0.5, 3000.0, 0.85, 2e-4, 0)
+
 WORKLOADS = {w.name: w for w in (WL_2D_128_FP64, WL_2D_512_FP32, WL_3D_256_FP32,
-                                 WL_2D_4096_FP32)}
+                                 WL_2D_4096_FP32, WL_3D_512_FP32)}
 
 
 def batch_specs(count: int = 64, seed: int = 0, dt: float = 5e-4) -> list:

@@ -35,7 +35,8 @@ ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECU
 
 # Every entry point declared in include/rotgp.h.
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
-           "rotgp_set_omega", "rotgp_init_analytic", "rotgp_set_psi", "rotgp_get_psi",
+           "rotgp_set_omega", "rotgp_init_analytic", "rotgp_init_analytic_field",
+           "rotgp_set_psi", "rotgp_get_psi",
            "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
            "rotgp_info", "rotgp_tune", "rotgp_set_solver", "rotgp_autotune",
            "rotgp_check_bounded_wait",
@@ -115,8 +116,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_last_error.restype = ctypes.c_char_p
         lib.rotgp_set_phys.argtypes = [vp, ctypes.POINTER(Phys)]
         lib.rotgp_set_omega.argtypes = [vp, ctypes.c_double]
-        lib.rotgp_init_analytic.argtypes = [vp, ip, dp, ctypes.c_double, ctypes.c_double]
-        lib.rotgp_set_psi.argtypes = [vp, vp, ip, ip]
+        lib.rotgp_init_analytic.argtypes = [vp, ip, ip, ctypes.c_ulonglong, ctypes.c_double,
+                                            ctypes.c_double]
+        lib.rotgp_init_analytic_field.argtypes = [vp, ip, dp, ctypes.c_double, ctypes.c_double]
+        lib.rotgp_set_psi.argtypes = [vp, vp, ip, ip, ip]
         lib.rotgp_get_psi.argtypes = [vp, vp, ip, ip]
         lib.rotgp_step_imag.argtypes = [vp, ctypes.c_longlong]
         lib.rotgp_step_real.argtypes = [vp, ctypes.c_longlong]
@@ -226,20 +229,33 @@ class Solver:
         self.phys.omega = float(omega)
 
     # -- state
-    def init_analytic(self, function: int = 1, phase_R=None, d_xy: float = 1.0, d_z: float = 1.0):
+    def init_analytic(self, function: int = 1, phase_R=None, d_xy: float = 1.0, d_z: float = 1.0,
+                      *, seed=None):
+        """Eq. fun.  ``seed``: the library draws R from SplitMix64(seed)
+        (``rotgp_init_analytic``); else ``phase_R`` is the (N_y+1, N_x+1)
+        array R or None (``rotgp_init_analytic_field``)."""
+        if seed is not None:
+            if phase_R is not None:
+                raise ValueError("give either seed or phase_R")
+            self._check(self._lib.rotgp_init_analytic(self._h, int(function), 1,
+                                                      int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                                      float(d_xy), float(d_z)))
+            return
         ptr = None
         if phase_R is not None:
             phase_R = np.ascontiguousarray(phase_R, dtype=np.float64)
             if phase_R.shape != (self.n[1] + 1, self.n[0] + 1):
                 raise ValueError("phase_R must have shape (N_y+1, N_x+1)")
             ptr = phase_R.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        self._check(self._lib.rotgp_init_analytic(self._h, int(function), ptr, float(d_xy),
-                                                  float(d_z)))
+        self._check(self._lib.rotgp_init_analytic_field(self._h, int(function), ptr,
+                                                        float(d_xy), float(d_z)))
 
-    def set_psi(self, psi):
-        """psi: numpy complex64/complex128 array or a CUDA torch complex tensor."""
+    def set_psi(self, psi, normalise: bool = False):
+        """psi: numpy complex64/complex128 array or a CUDA torch complex tensor;
+        ``normalise`` renormalises it to unit norm."""
         ptr, on_dev, is64, _keep = _buffer(psi, self.shape)
-        self._check(self._lib.rotgp_set_psi(self._h, ctypes.c_void_p(ptr), on_dev, is64))
+        self._check(self._lib.rotgp_set_psi(self._h, ctypes.c_void_p(ptr), on_dev, is64,
+                                            int(bool(normalise))))
 
     def get_psi(self, out=None, fp64: bool = True):
         """Return the state as numpy (or fill ``out``: numpy or CUDA torch tensor)."""

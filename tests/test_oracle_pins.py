@@ -489,3 +489,53 @@ def test_fourth_order_forms_share_the_interaction_term():
     psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(n[0], n[1], 4))
     ob = oracle.observables(grid, phys, psi)
     assert abs((ob["mu4"] - ob["energy4"]) - (ob["mu_c"] - ob["energy_c"])) < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.4, 1.1, 2.6, np.pi / 2 - 0.01])
+@pytest.mark.parametrize("shape", [(24, 20), (14, 12, 10)])
+def test_real_part_forms_equal_complex_forms_on_a_phase_times_real_state(theta, shape):
+    """For psi = e^{i theta} f with f real, the real-part forms of Eqs.
+    e2dr/e3dr equal the complex forms of Eqs. e2d/e3d at any g and Omega:
+    psi_R = cos(theta) f, so the interaction weight sum |psi|^2 psi_R^2 /
+    sum psi_R^2 is sum f^4 / sum f^2 for both, and the rotation terms vanish
+    in both because y D_x - x D_y is antisymmetric.  A wrong alpha (g/2 in E,
+    g in mu), a wrong interaction weight or a wrong rotation sign in the
+    real-part forms fails this.  theta close to pi/2 exercises the -i guard."""
+    dim = len(shape)
+    h = (0.4, 0.45, 0.5)[:dim]
+    grid = Grid(shape, h)
+    phys = Phys(gamma=1.0, nu=1.15, lam=1.3, g=37.0, omega=0.6, dt=2e-3)
+    # f = |psi| of a rotating, interacting state (real and non-negative)
+    psi = oracle.init_analytic(grid, 1, inputs.random_phase_field(shape[0], shape[1], 5))
+    psi, _ = oracle.steps(grid, phys, psi, 60, True)
+    f = np.abs(psi) * (1.0 + 0.2 * np.cos(np.arange(psi.size).reshape(psi.shape) * 0.37))
+    state = np.exp(1j * theta) * f
+    ob = oracle.observables(grid, phys, state)
+    for a, b in (("energy", "energy_c"), ("mu", "mu_c")):
+        assert abs(ob[a] - ob[b]) < 1e-12 * abs(ob[b]), (a, ob[a], ob[b])
+    # the interaction contributes: the same state at g = 0 is far away
+    ob0 = oracle.observables(grid, Phys(gamma=1.0, nu=1.15, lam=1.3, g=0.0, omega=0.6), state)
+    assert abs(ob["energy"] - ob0["energy"]) > 0.1 and abs(ob["mu"] - ob0["mu"]) > 0.2
+
+
+@pytest.mark.parametrize("shape", [(40, 36), (20, 18, 12)])
+def test_initial_state_carries_the_random_phase_two_pi_r(shape):
+    """Eq. fun multiplies the analytic state by exp(2 pi i R(x, y)): the phase
+    of psi conj(psi without R) is 2 pi R_ij (mod 2 pi) at every interior point
+    (i, j), the same on every z plane in 3D.  A phase of R instead of 2 pi R,
+    or R indexed with x and y swapped, fails this."""
+    dim = len(shape)
+    grid = Grid(shape, (0.3, 0.25, 0.4)[:dim])
+    R = inputs.random_phase_field(shape[0], shape[1], 11)
+    psi = oracle.init_analytic(grid, 1, R, normalize=False)
+    plain = oracle.init_analytic(grid, 1, None, normalize=False)
+    prod = psi * np.conj(plain)
+    ok = np.abs(plain) > 1e-12 * np.max(np.abs(plain))
+    want = np.broadcast_to(R, prod.shape)  # R[j, i], x fastest; z planes share it
+    d = np.angle(prod) - 2 * np.pi * want
+    d = (d + np.pi) % (2 * np.pi) - np.pi
+    assert ok.sum() > 0.5 * ok.size
+    assert np.max(np.abs(d[ok])) < 1e-12
+    # R is not symmetric, so a transposed index would not pass
+    assert np.max(np.abs(R[:shape[0] + 1 - 4, :shape[0] + 1 - 4] -
+                         R[:shape[0] + 1 - 4, :shape[0] + 1 - 4].T)) > 0.1

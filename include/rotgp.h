@@ -44,8 +44,8 @@ extern "C" {
 #define ROTGP_ENOMEM (-2)       /* device or host allocation failed          */
 #define ROTGP_ECUDA (-3)        /* a CUDA runtime call or launch failed      */
 #define ROTGP_ENONFINITE (-4)   /* NaN/Inf norm seen by the step reduction   */
-#define ROTGP_EUNSUPPORTED (-5) /* line systems too weakly diagonally
-                                   dominant for the chunked line solver      */
+#define ROTGP_EUNSUPPORTED (-5) /* form or shape not available for this
+                                   context (see the call)                    */
 #define ROTGP_ETIMEOUT (-6)     /* a bounded device wait (TMA load) ran out  */
 
 #define ROTGP_FP64 0 /* complex double throughout                           */
@@ -119,15 +119,19 @@ typedef struct {
   int warps_per_block[3];
   int fused_xy;           /* 1: H1 and the x and y sweeps run as one tile
                              pass (ROTGP_SOLVER_FUSED)                    */
+  int hybrid_cluster[3];  /* CTAs sharing one line in the exact partition
+                             solve (ROTGP_SOLVER_HYBRID), 0 if not used   */
   double decay;           /* largest per-point decay of a truncated carry */
   size_t device_bytes;    /* device memory owned by the context           */
 } rotgp_solver_info;
 
 /* Create a context for one condensate on the current CUDA device; stream is
  * a cudaStream_t (NULL = legacy default stream).  The state is zero until
- * rotgp_init_analytic or rotgp_set_psi.  Fails with ROTGP_EUNSUPPORTED if
- * Delta/h^2 is so large that a truncated line carry decays too slowly
- * (chunk halo above 64 points). */
+ * rotgp_init_analytic or rotgp_set_psi.  When Delta/h^2 is so large that a
+ * truncated line carry decays too slowly (chunk halo above 64 points) every
+ * sweep takes the exact partition solve (ROTGP_SOLVER_HYBRID); fails with
+ * ROTGP_EUNSUPPORTED if that has no tile shape for the line length, or if the
+ * Thomas multipliers do not reach their fixed point within 512 points. */
 int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision,
                  void* stream, rotgp_ctx** out);
 void rotgp_destroy(rotgp_ctx* ctx);
@@ -207,7 +211,10 @@ int rotgp_info(const rotgp_ctx* ctx, rotgp_solver_info* out);
  * steps of an axis so tuned run the default two-lines-per-thread form, whose
  * folded weights keep the CN map's norm to float rounding.  Changes speed only: every shape gives results
  * equal up to the truncation bound of the chunked line solver.  Used by the
- * autotuner.  ROTGP_EINVAL for a shape that is not built or does not fit. */
+ * autotuner.  On an axis in the exact partition solve (ROTGP_SOLVER_HYBRID)
+ * only `segments` applies: the number of CTAs (1, 2, 4 or 8, one cluster)
+ * that share each line; results are equal up to rounding.
+ * ROTGP_EINVAL for a shape that is not built or does not fit. */
 int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring,
                int warps_per_block, int segments);
 
@@ -229,13 +236,28 @@ int rotgp_tune(rotgp_ctx* ctx, int axis, int lines_per_lane, int chunk, int ring
  * steps always use the Thomas form, whose Crank-Nicolson map stays unitary
  * with rounded coefficients (independently rounded stencil weights would
  * let the norm drift by ~1e-7 per step in float).
- * A new context uses ROTGP_SOLVER_THOMAS on every axis. 
+ * ROTGP_SOLVER_HYBRID: the same Thomas solution of every whole line with
+ *   nothing truncated, by a partition method: each line is cut into
+ *   segments that run the Thomas recurrences locally from zero carries, the
+ *   true carries follow from composing the segments' affine summaries (the
+ *   reduced system), and the segments rerun from them.  A line lives in the
+ *   shared memory of one CTA or of a cluster of up to 8 CTAs (distributed
+ *   shared memory), so each point is read and written once per sweep;
+ *   complex float and double, both propagation modes.  It serves long lines
+ *   whose carries decay slowly (a truncation halo of more than 16 points),
+ *   and it is the only form when they decay too slowly for any truncation
+ *   (halo above 64 points).  ROTGP_EUNSUPPORTED when the line is too long
+ *   for a cluster of 8 tiles of about 200 KB.
+ * A new context uses ROTGP_SOLVER_THOMAS on every axis, except that complex
+ * float axes with a halo above 16 points take ROTGP_SOLVER_HYBRID, and every
+ * axis does when the halo exceeds 64 points. 
  * The y and z sweeps in stencil form, and the fused pass, stage their
  * tiles with TMA loads whose waits are bounded: a wait that runs out
  * (about 2 s) makes the next synchronising call return ROTGP_ETIMEOUT. */
 #define ROTGP_SOLVER_THOMAS 0
 #define ROTGP_SOLVER_STENCIL 1
 #define ROTGP_SOLVER_FUSED 2
+#define ROTGP_SOLVER_HYBRID 3
 int rotgp_set_solver(rotgp_ctx* ctx, int axis, int solver);
 
 /* Pick the fastest line-solver forms for this context by timing them.
@@ -248,7 +270,9 @@ int rotgp_set_solver(rotgp_ctx* ctx, int axis, int solver);
  * state, timed with CUDA events on the context's stream (the faster repeat
  * counts); the state, its pending renormalisation and the step counter are
  * restored afterwards, and the fastest candidate stays selected.  *choice (if not NULL) receives it as a bit set: bit a =
- * axis a in stencil form, bit 3 = fused x-y pass.  Synchronises the stream.
+ * axis a in stencil form, bit 3 = fused x-y pass, bit 4 + a = axis a in the
+ * exact partition solve (candidates include every supported combination
+ * with it).  Synchronises the stream.
  * ROTGP_EINVAL if steps < 1. */
 int rotgp_autotune(rotgp_ctx* ctx, int steps, int* choice);
 

@@ -182,6 +182,20 @@ cudaError_t launch_sweep_strided(bool fp64, bool reduce, const stream_args& a,
                                  int axis, cudaStream_t s);
 // blocks of the one-line-per-lane strided form with one warp per block
 long long strided1_blocks(long long nlines, int nx, int nseg);
+// Exact partition-method line solve of one sweep (hybrid.cu): axis 0 (x,
+// with H1 and the pending scale fused in), 1 (y) or 2 (z); clusters of cs
+// CTAs, each a tile of 16 lines x pc positions, lsub positions per thread;
+// reduce: the norm epilogue of the last sweep of a step.
+cudaError_t launch_line_hybrid(bool fp64, bool imag, bool reduce, int axis, const stream_args& a,
+                               int cs, int pc, int lsub, cudaStream_t s);
+// tile shape for lines of N points within max_bytes of shared memory per CTA
+bool hybrid_shape(int N, int axis, bool fp64, size_t max_bytes, int* cs, int* pc, int* lsub);
+// the tile of a given cluster size; returns its shared-memory bytes
+size_t hybrid_tile(int N, int axis, bool fp64, int cs, int* pc, int* lsub);
+// line groups (tiles of 16 lines) of an axis
+long long hybrid_groups(int axis, long long nlines, int nx);
+// clusters of that shape resident at once on the current device (0: none)
+int hybrid_max_clusters(bool fp64, int axis, int cs, int pc);
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);
 // Launch with programmatic stream serialization: the kernel's blocks may be
 // scheduled while the previous kernel in the stream finishes; the kernel

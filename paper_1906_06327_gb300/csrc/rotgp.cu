@@ -62,6 +62,11 @@ struct AxisPlan {
   int sK = 0, sB = 0;
   int lsegs = 1;  // segments per line of the stencil line pass (y, z)
   void* wtab[2] = {nullptr, nullptr};
+  // exact partition-method solve (hybrid.cu): clusters of hcs CTAs, each a
+  // tile of 16 lines x hpc positions, hlsub positions per thread
+  bool hyb_ok = false;
+  bool use_hybrid = false;
+  int hcs = 1, hpc = 0, hlsub = 0;
 };
 
 struct ProfRec {
@@ -84,6 +89,7 @@ struct rotgp_ctx {
   // solver sizing
   int halo = 2, lt = 8;
   double decay = 0;
+  bool chunk_ok = true;  // carries decay fast enough for the chunked solver
   // device memory
   void* psi[2] = {nullptr, nullptr};
   int cur = 0;
@@ -180,7 +186,7 @@ axis_coef make_coef(int axis, int imag, double h, double dt, double omega, doubl
 // Worst-case carry decay and multiplier-table length over the lines of an
 // axis: iterate c'_p = A+ / (A0 - A- c'_{p-1}) to its fixed point c*, then
 // forward decay |A- m*|, backward decay |c*|.
-void size_axis(const axis_coef& co, int nlines, double* decay, int* lt) {
+void size_axis(const axis_coef& co, int nlines, double* decay, int* lt, bool* converged) {
   for (int l = 0; l < nlines; ++l) {
     const double u = co.u0 + l * co.du;
     const cd kap(co.kap_re, co.kap_im), tau = cd(co.tau_re, co.tau_im) * u;
@@ -194,6 +200,7 @@ void size_axis(const axis_coef& co, int nlines, double* decay, int* lt) {
       c = cn;
       if (conv) break;
     }
+    if (p > kMaxTable) *converged = false;
     *lt = std::max(*lt, std::min(p + 1, kMaxTable));
     *decay = std::max(*decay, std::max(std::abs(am * m), std::abs(c)));
   }
@@ -206,16 +213,19 @@ double nlines_du(const rotgp_ctx* c, int axis) {
   return axis == 0 ? c->grid.h[1] : (axis == 1 ? c->grid.h[0] : 0.0);
 }
 
-// Size the line solver for the current physics (both modes).
-int plan_solver(rotgp_ctx* c, int* halo, int* lt, double* decay) {
+// Size the line solver for the current physics (both modes).  A halo above
+// kMaxHalo leaves only the exact partition solve (hybrid.cu), which needs the
+// table of every line to reach its fixed point (the Toeplitz interior).
+int plan_solver(rotgp_ctx* c, int* halo, int* lt, double* decay, bool* chunk_ok) {
   double dec = 0;
   int tl = 2;
+  bool conv = true;
   for (int a = 0; a < c->grid.dim; ++a) {
     const int nl = a == 0 ? c->ny : (a == 1 ? c->nx : 1);
     for (int mode = 0; mode < 2; ++mode) {
       axis_coef co = make_coef(a, mode, c->grid.h[a], c->phys.dt, c->phys.omega,
                                nlines_u0(c, a), nlines_du(c, a));
-      size_axis(co, nl, &dec, &tl);
+      size_axis(co, nl, &dec, &tl, &conv);
     }
   }
   if (!(dec < 1.0) || !std::isfinite(dec))
@@ -223,11 +233,15 @@ int plan_solver(rotgp_ctx* c, int* halo, int* lt, double* decay) {
   const double tol = c->fp64 ? 1e-17 : 1e-9;
   int H = dec <= 0 ? 1 : (int)std::ceil(std::log(tol) / std::log(dec)) + 1;
   H = std::max(H, 2);
-  if (H > kMaxHalo)
-    return fail(c, ROTGP_EUNSUPPORTED,
-                "chunk halo %d > %d: Delta/h^2 too large for the chunked line solver "
-                "(carry decay factor %.3f)",
-                H, kMaxHalo, dec);
+  *chunk_ok = H <= kMaxHalo;
+  if (!*chunk_ok) {
+    if (!conv)
+      return fail(c, ROTGP_EUNSUPPORTED,
+                  "line coefficients do not reach their fixed point within %d points "
+                  "(carry decay factor %.4f): Delta/h^2 too large",
+                  kMaxTable, dec);
+    H = kMaxHalo;
+  }
   *halo = H;
   *lt = tl;
   *decay = dec;
@@ -374,6 +388,32 @@ int plan_axes(rotgp_ctx* c) {
     ap.len = a == 0 ? c->nx : (a == 1 ? c->ny : c->nz);
     ap.lines = a == 0 ? (long long)c->ny * c->nz
                       : (a == 1 ? (long long)c->nx * c->nz : (long long)c->nx * c->ny);
+    // exact partition solve: tiles of at most ~100 KB (two or three CTAs per
+    // SM), else up to ~200 KB, in clusters of at most 8 CTAs
+    ap.hyb_ok = false;
+    for (size_t budget : {(size_t)100 * 1024, (size_t)200 * 1024}) {
+      int cs = 0, pc = 0, ls = 0;
+      if (budget > (size_t)c->smem_optin - 16 * 1024) break;
+      if (!hybrid_shape(ap.len, a, c->fp64, budget, &cs, &pc, &ls)) continue;
+      if (hybrid_max_clusters(c->fp64, a, cs, pc) < 1) continue;
+      ap.hyb_ok = true;
+      ap.hcs = cs;
+      ap.hpc = pc;
+      ap.hlsub = ls;
+      break;
+    }
+    if (!c->chunk_ok) {
+      // carries too slow for any truncation: the exact solve on every axis
+      if (!ap.hyb_ok)
+        return fail(c, ROTGP_EUNSUPPORTED,
+                    "carry decay %.4f needs the exact line solve, which has no tile shape "
+                    "for %d points per line",
+                    c->decay, ap.len);
+      ap.use_hybrid = true;
+      ap.use_stencil = false;
+      ap.stencil_ok = false;
+      continue;
+    }
     int V = 1, C = c->halo <= 16 ? 16 : 64;
     if (!c->fp64 && c->halo <= 16 && (x || c->nx % 2 == 0)) {
       V = 2;
@@ -418,12 +458,18 @@ int plan_axes(rotgp_ctx* c) {
       }
     }
     // default: the Thomas form (the stencil and fused forms are selected by
-    // rotgp_set_solver or rotgp_autotune)
+    // rotgp_set_solver or rotgp_autotune), except that complex-float lines
+    // too long-range for the chunk-8/16 forms take the exact partition solve
     ap.use_stencil = false;
+    ap.use_hybrid = !c->fp64 && c->halo > 16 && ap.hyb_ok;
   }
   // one pass for H1, x and y: both axes in stencil form with one reach K
   // (the larger of the two; a longer stencil is only more exact)
   AxisPlan &ax = c->axis[0], &ay = c->axis[1];
+  if (!c->chunk_ok) {
+    c->fuse_ok = c->fuse_xy = false;
+    return ROTGP_OK;
+  }
   if (!ax.wtab[0] && ax.stencil_ok && ay.stencil_ok) {
     const int K = std::max(ax.sK, ay.sK);
     ax.sK = ay.sK = K;
@@ -690,6 +736,29 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
   a.taps_k = ap.sK;
   a.brows = ap.sB;
   cudaError_t e;
+  if (ap.use_hybrid) {
+    // exact partition solve, every precision and mode (H1 fused into x)
+    a.coef_mode = axis == 0 ? 2 : (axis == 1 ? 1 : 0);
+    a.stride = axis == 1 ? (long long)c->nx : (long long)c->nx * c->ny;
+    a.outer = axis == 1 ? (long long)c->nx * c->ny : (long long)c->nx;
+    a.dt = c->phys.dt;
+    a.g = c->phys.g;
+    a.hgam2 = 0.5 * c->phys.gamma * c->phys.gamma;
+    a.hnu2 = 0.5 * c->phys.nu * c->phys.nu;
+    a.hlam2 = c->grid.dim == 3 ? 0.5 * c->phys.lambda * c->phys.lambda : 0.0;
+    a.x0 = c->x0;
+    a.hx = c->grid.h[0];
+    a.y0 = c->y0;
+    a.hy = c->grid.h[1];
+    a.z0 = c->z0;
+    a.hz = c->grid.dim == 3 ? c->grid.h[2] : 0.0;
+    a.scale = c->d_scale();
+    Timed t(c, axis == 0 ? K_SWEEP_X : (axis == 1 ? K_SWEEP_Y : K_SWEEP_Z));
+    e = launch_line_hybrid(c->fp64, imag, last, axis, a, ap.hcs, ap.hpc, ap.hlsub, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hybrid sweep launch");
+    c->cur = 1 - c->cur;
+    return ROTGP_OK;
+  }
   if (axis == 0) {
     a.coef_mode = 2;
     a.dt = c->phys.dt;
@@ -950,7 +1019,8 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     delete c;
     return rc;
   }
-  int rc = plan_solver(c, &c->halo, &c->lt, &c->decay);
+  // the decay factor is needed by plan_axes' messages
+  int rc = plan_solver(c, &c->halo, &c->lt, &c->decay, &c->chunk_ok);
   if (!rc) rc = plan_axes(c);
   if (rc) {
     g_create_error = c->err;
@@ -972,6 +1042,13 @@ int rotgp_create(const rotgp_grid* grid, const rotgp_phys* phys, int precision, 
     pd = std::max(pd, (size_t)strided1_blocks(last.lines, c->nx, (int)nch));
   }
   pd = std::max(pd, (size_t)reduce_blocks(c, (long long)c->nx * c->ny) * 3);
+  {
+    // the exact partition solve of the last axis: one block per tile
+    const int la = grid->dim - 1;
+    const AxisPlan& last = c->axis[la];
+    if (last.hyb_ok)
+      pd = std::max(pd, (size_t)(hybrid_groups(la, last.lines, c->nx) * 8));
+  }
   c->partial_doubles = pd;
   c->staging_bytes = (size_t)(grid->n[0] + 1) * (grid->n[1] + 1) *
                      (grid->dim == 3 ? grid->n[2] + 1 : 1) * 16;
@@ -1060,7 +1137,27 @@ int rotgp_set_phys(rotgp_ctx* c, const rotgp_phys* phys) {
   c->phys = *phys;
   int halo = 0, lt = 0;
   double dec = 0;
-  int rc = plan_solver(c, &halo, &lt, &dec);
+  bool chunk_ok = true;
+  const bool old_chunk_ok = c->chunk_ok;
+  int rc = plan_solver(c, &halo, &lt, &dec, &chunk_ok);
+  if (!rc && chunk_ok != old_chunk_ok) {
+    // switch between the chunked and the exact-only plans
+    c->chunk_ok = chunk_ok;
+    const int old_h = c->halo;
+    c->halo = std::max(halo, c->halo);
+    rc = lt > c->lt ? fail(c, ROTGP_EUNSUPPORTED,
+                           "new physics needs %d table entries (context has %d)", lt, c->lt)
+                    : plan_axes(c);
+    if (rc) {
+      c->chunk_ok = old_chunk_ok;
+      c->halo = old_h;
+      c->phys = old;
+      plan_axes(c);
+      return rc;
+    }
+    c->decay = std::max(c->decay, dec);
+    return build_tables(c);
+  }
   if (!rc && lt > c->lt) {
     // tables were sized at create; a longer table needs more memory
     rc = fail(c, ROTGP_EUNSUPPORTED, "new physics needs %d table entries (context has %d)", lt,
@@ -1279,11 +1376,15 @@ int rotgp_info(const rotgp_ctx* c, rotgp_solver_info* out) {
     const bool on = a < c->grid.dim;
     out->chunk[a] = on ? c->axis[a].sh.C : 0;
     out->segments[a] =
-        on ? (a >= 1 && c->axis[a].use_stencil ? c->axis[a].lsegs : c->axis[a].nseg) : 0;
+        on ? (c->axis[a].use_hybrid ? c->axis[a].hcs
+                                    : (a >= 1 && c->axis[a].use_stencil ? c->axis[a].lsegs
+                                                                        : c->axis[a].nseg))
+           : 0;
     out->lines_per_lane[a] = on ? c->axis[a].sh.V : 0;
     out->ring[a] = on ? c->axis[a].sh.R : 0;
     out->stencil_taps[a] = on && c->axis[a].use_stencil ? 2 * c->axis[a].sK + 1 : 0;
     out->warps_per_block[a] = on ? c->axis[a].sh.warps_per_block : 0;
+    out->hybrid_cluster[a] = on && c->axis[a].use_hybrid ? c->axis[a].hcs : 0;
   }
   out->table_len = c->lt;
   out->fused_xy = c->fuse_xy ? 1 : 0;
@@ -1305,6 +1406,25 @@ int rotgp_tune(rotgp_ctx* c, int axis, int lines_per_lane, int chunk, int ring,
     return ROTGP_OK;
   }
   if (axis < 0 || axis >= c->grid.dim) return fail(c, ROTGP_EINVAL, "axis out of range");
+  if (c->axis[axis].use_hybrid) {
+    // exact partition solve: only the segment count applies, as the number
+    // of CTAs (one cluster) that share each line
+    AxisPlan& ap = c->axis[axis];
+    if (segments != 1 && segments != 2 && segments != 4 && segments != 8)
+      return fail(c, ROTGP_EINVAL, "the exact solve splits a line over 1, 2, 4 or 8 CTAs");
+    int pc = 0, ls = 0;
+    const size_t bytes = hybrid_tile(ap.len, axis, c->fp64, segments, &pc, &ls);
+    if (bytes > (size_t)c->smem_optin - 16 * 1024 ||
+        hybrid_max_clusters(c->fp64, axis, segments, pc) < 1)
+      return fail(c, ROTGP_EINVAL, "a line of %d points does not fit %d CTAs", ap.len, segments);
+    if (axis == c->grid.dim - 1 &&
+        (size_t)(hybrid_groups(axis, ap.lines, c->nx) * segments) > c->partial_doubles)
+      return fail(c, ROTGP_EINVAL, "%d CTAs per line exceed the reduction buffer", segments);
+    ap.hcs = segments;
+    ap.hpc = pc;
+    ap.hlsub = ls;
+    return ROTGP_OK;
+  }
   if (warps_per_block < 1 || warps_per_block > 8)
     return fail(c, ROTGP_EINVAL, "warps_per_block must be 1..8");
   if (segments < 1) return fail(c, ROTGP_EINVAL, "segments must be >= 1");
@@ -1322,14 +1442,26 @@ int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
   ++c->plan_version;
   if (axis < 0 || axis >= c->grid.dim) return fail(c, ROTGP_EINVAL, "axis out of range");
   if (solver != ROTGP_SOLVER_THOMAS && solver != ROTGP_SOLVER_STENCIL &&
-      solver != ROTGP_SOLVER_FUSED)
+      solver != ROTGP_SOLVER_FUSED && solver != ROTGP_SOLVER_HYBRID)
     return fail(c, ROTGP_EINVAL, "unknown solver %d", solver);
   AxisPlan& ap = c->axis[axis];
+  if (solver == ROTGP_SOLVER_HYBRID) {
+    if (!ap.hyb_ok)
+      return fail(c, ROTGP_EUNSUPPORTED, "no exact line-solve tile for axis %d", axis);
+    ap.use_hybrid = true;
+    ap.use_stencil = false;
+    if (axis <= 1) c->fuse_xy = false;
+    return ROTGP_OK;
+  }
+  if (!c->chunk_ok)
+    return fail(c, ROTGP_EUNSUPPORTED,
+                "the line carries decay too slowly for any form but the exact solve");
   if (solver == ROTGP_SOLVER_FUSED) {
     if (axis > 1) return fail(c, ROTGP_EINVAL, "the fused pass covers the x and y sweeps only");
     if (!c->fuse_ok)
       return fail(c, ROTGP_EUNSUPPORTED, "no fused x-y pass for this context");
     c->axis[0].use_stencil = c->axis[1].use_stencil = true;
+    c->axis[0].use_hybrid = c->axis[1].use_hybrid = false;
     c->fuse_xy = true;
     return ROTGP_OK;
   }
@@ -1337,6 +1469,7 @@ int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
       (!ap.stencil_ok || (axis == 0 && c->nx % 4 != 0 && !c->xpass_ok)))
     return fail(c, ROTGP_EUNSUPPORTED, "no stencil form for axis %d of this context", axis);
   ap.use_stencil = solver == ROTGP_SOLVER_STENCIL;
+  ap.use_hybrid = false;
   if (axis <= 1) c->fuse_xy = false;
   return ROTGP_OK;
 }
@@ -1346,7 +1479,8 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
   ++c->plan_version;
   if (steps < 1) return fail(c, ROTGP_EINVAL, "steps must be >= 1");
   const int dim = c->grid.dim;
-  // candidate forms: bit a = axis a in stencil form, bit 3 = fused x-y pass
+  // candidate forms: bit a = axis a in stencil form, bit 3 = fused x-y pass,
+  // bit 4 + a = axis a in the exact partition solve
   std::vector<int> cand;
   for (int m = 0; m < (1 << dim); ++m) {
     bool ok = true;
@@ -1359,9 +1493,26 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
     cand.push_back(8 | 3);
     if (dim == 3 && c->axis[2].stencil_ok) cand.push_back(8 | 7);
   }
+  {
+    // each candidate again with any of its Thomas axes in the exact solve
+    const size_t nbase = cand.size();
+    for (size_t i = 0; i < nbase; ++i)
+      for (int h = 1; h < (1 << dim); ++h) {
+        bool ok = true;
+        for (int a = 0; a < dim; ++a)
+          if ((h >> a) & 1)
+            ok = ok && c->axis[a].hyb_ok && !((cand[i] >> a) & 1) &&
+                 !((cand[i] & 8) && a <= 1);
+        if (ok) cand.push_back(cand[i] | (h << 4));
+      }
+    if (!c->chunk_ok) cand.assign(1, ((1 << dim) - 1) << 4);
+  }
   auto apply = [&](int m) {
     c->fuse_xy = (m & 8) != 0;
-    for (int a = 0; a < dim; ++a) c->axis[a].use_stencil = ((m >> a) & 1) != 0;
+    for (int a = 0; a < dim; ++a) {
+      c->axis[a].use_stencil = ((m >> a) & 1) != 0;
+      c->axis[a].use_hybrid = ((m >> (4 + a)) & 1) != 0;
+    }
   };
   // save the state, its pending scale and the counters
   const size_t state = (size_t)c->sites * c->elem;
@@ -1420,7 +1571,7 @@ int rotgp_autotune(rotgp_ctx* c, int steps, int* choice) {
   // number of warps decides how many waves of resident warps a launch takes)
   for (int ax = 0; ax < dim && e == cudaSuccess && !rc; ++ax) {
     AxisPlan& ap = c->axis[ax];
-    if (ap.use_stencil || (ax <= 1 && c->fuse_xy)) continue;
+    if (ap.use_stencil || ap.use_hybrid || (ax <= 1 && c->fuse_xy)) continue;
     // lines per lane, chunk length and segment count together (they decide
     // the warp count and the warm-up overhead jointly), then the ring depth
     for (int phase = 0; phase < 2 && e == cudaSuccess && !rc; ++phase) {

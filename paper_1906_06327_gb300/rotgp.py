@@ -28,6 +28,7 @@ ROTGP_FP32 = 1
 ROTGP_SOLVER_THOMAS = 0
 ROTGP_SOLVER_STENCIL = 1
 ROTGP_SOLVER_FUSED = 2
+ROTGP_SOLVER_HYBRID = 3
 
 ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECUDA",
                ROTGP_ENONFINITE: "ENONFINITE", ROTGP_EUNSUPPORTED: "EUNSUPPORTED",
@@ -78,6 +79,7 @@ class SolverInfo(ctypes.Structure):
                 ("lines_per_lane", ctypes.c_int * 3), ("ring", ctypes.c_int * 3),
                 ("stencil_taps", ctypes.c_int * 3),
                 ("warps_per_block", ctypes.c_int * 3), ("fused_xy", ctypes.c_int),
+                ("hybrid_cluster", ctypes.c_int * 3),
                 ("decay", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
 
 
@@ -300,15 +302,16 @@ class Solver:
         ch = ctypes.c_int(0)
         self._check(self._lib.rotgp_autotune(self._h, int(steps), ctypes.byref(ch)))
         m = ch.value
-        form = ["stencil" if (m >> a) & 1 else "thomas" for a in range(self.dim)]
+        form = ["stencil" if (m >> a) & 1 else "hybrid" if (m >> (4 + a)) & 1 else "thomas"
+                for a in range(self.dim)]
         if m & 8:
             form[0] = form[1] = "fused"
         return {"choice": m, "forms": form}
 
     def set_solver(self, axis: int, solver: str):
-        """solver: "thomas", "stencil" or "fused" (see rotgp_set_solver)."""
+        """solver: "thomas", "stencil", "fused" or "hybrid" (see rotgp_set_solver)."""
         code = {"thomas": ROTGP_SOLVER_THOMAS, "stencil": ROTGP_SOLVER_STENCIL,
-                "fused": ROTGP_SOLVER_FUSED}[solver]
+                "fused": ROTGP_SOLVER_FUSED, "hybrid": ROTGP_SOLVER_HYBRID}[solver]
         self._check(self._lib.rotgp_set_solver(self._h, int(axis), code))
 
     # -- timing

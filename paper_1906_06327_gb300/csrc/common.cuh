@@ -196,6 +196,8 @@ size_t hybrid_tile(int N, int axis, bool fp64, int cs, int* pc, int* lsub);
 long long hybrid_groups(int axis, long long nlines, int nx);
 // clusters of that shape resident at once on the current device (0: none)
 int hybrid_max_clusters(bool fp64, int axis, int cs, int pc);
+// the host step of the last hybrid launch on this thread (error messages)
+const char* hybrid_launch_stage();
 size_t sweep_smem_per_warp(bool fp64, bool x_sweep, int V, int C, int R);
 // Launch with programmatic stream serialization: the kernel's blocks may be
 // scheduled while the previous kernel in the stream finishes; the kernel

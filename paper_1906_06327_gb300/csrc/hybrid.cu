@@ -89,6 +89,14 @@ __global__ void __launch_bounds__(kHThreads) k_line_hybrid(const hybrid_args ha)
 
   cg::cluster_group cluster = cg::this_cluster();
   const int cs = ha.cs, pc = ha.pc, lsub = ha.lsub;
+  // a tile of whole lines (cs = 1) is launched without a cluster: no cluster
+  // barrier and no remote shared memory then
+  auto csync = [&]() {
+    if (cs > 1)
+      cluster.sync();
+    else
+      __syncthreads();
+  };
   const int rank = (int)(blockIdx.x % (unsigned)cs);
   const long long grp = blockIdx.x / (unsigned)cs;
   const int W = pc + 4;          // tile positions incl. 2 halo points either side
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(kHThreads) k_line_hybrid(const hybrid_args ha)
     xG[ln] = Gc;
     xD[ln] = Dc;
   }
-  cluster.sync();
+  csync();
   if (tid < kHL) {
     const int ln = tid;
     E carry = zero<T>();
@@ -290,7 +298,7 @@ __global__ void __launch_bounds__(kHThreads) k_line_hybrid(const hybrid_args ha)
     xB[ln] = Bc;
     xX[ln] = Xc;
   }
-  cluster.sync();
+  csync();
   if (tid < kHL) {
     const int ln = tid;
     E carry = zero<T>();
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(kHThreads) k_line_hybrid(const hybrid_args ha)
     }
   }
   // every CTA's remote reads are done before any CTA moves on (and exits)
-  cluster.sync();
+  csync();
 
   // ---- B2: backward from the true carry; x overwrites d in the tile
   acc_t<T> acc;
@@ -356,14 +364,23 @@ __global__ void __launch_bounds__(kHThreads) k_line_hybrid(const hybrid_args ha)
 
 namespace {
 
+thread_local const char* g_hybrid_stage = "";
+
 template <class T, int AX, bool H1, bool IMAG, bool REDUCE>
 cudaError_t launch_h(const hybrid_args& ha, cudaStream_t s) {
   auto fn = k_line_hybrid<T, AX, H1, IMAG, REDUCE>;
   const size_t smem = (size_t)kHL * (ha.pc + 4) * sizeof(cpx<T>);
+  g_hybrid_stage = "shared-memory opt-in";
   cudaError_t e = allow_smem_bytes((const void*)fn, (int)smem);
   if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)(ha.ngroups * ha.cs);
+  if (ha.cs == 1) {
+    g_hybrid_stage = "launch";
+    fn<<<blocks, kHThreads, smem, s>>>(ha);
+    return cudaGetLastError();
+  }
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)(ha.ngroups * ha.cs));
+  cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kHThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -374,6 +391,7 @@ cudaError_t launch_h(const hybrid_args& ha, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  g_hybrid_stage = "cluster launch";
   return cudaLaunchKernelEx(&cfg, fn, ha);
 }
 
@@ -434,6 +452,12 @@ int hybrid_max_clusters(bool fp64, int axis, int cs, int pc) {
                    : (const void*)k_line_hybrid<float, 1, false, false, true>;
   const size_t smem = hybrid_smem_bytes(pc, fp64);
   if (allow_smem_bytes(fn, (int)smem) != cudaSuccess) return 0;
+  if (cs == 1) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kHThreads, smem) != cudaSuccess)
+      return 0;
+    return nb;
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(cs * 64));
   cfg.blockDim = dim3(kHThreads);
@@ -449,6 +473,8 @@ int hybrid_max_clusters(bool fp64, int axis, int cs, int pc) {
   if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) return 0;
   return n;
 }
+
+const char* hybrid_launch_stage() { return g_hybrid_stage; }
 
 cudaError_t launch_line_hybrid(bool fp64, bool imag, bool reduce, int axis, const stream_args& a,
                                int cs, int pc, int lsub, cudaStream_t s) {

@@ -755,7 +755,9 @@ int sweep(rotgp_ctx* c, int axis, bool imag, bool last) {
     a.scale = c->d_scale();
     Timed t(c, axis == 0 ? K_SWEEP_X : (axis == 1 ? K_SWEEP_Y : K_SWEEP_Z));
     e = launch_line_hybrid(c->fp64, imag, last, axis, a, ap.hcs, ap.hpc, ap.hlsub, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "hybrid sweep launch");
+    if (e != cudaSuccess)
+      return fail(c, ROTGP_ECUDA, "hybrid sweep of axis %d (%s, %d CTAs per line, tile %d): %s",
+                  axis, hybrid_launch_stage(), ap.hcs, ap.hpc, cudaGetErrorString(e));
     c->cur = 1 - c->cur;
     return ROTGP_OK;
   }

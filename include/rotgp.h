@@ -188,6 +188,19 @@ int rotgp_get_psi(rotgp_ctx* ctx, void* dst, int dst_on_device, int dst_is_fp64)
 int rotgp_step_imag(rotgp_ctx* ctx, long long n);
 int rotgp_step_real(rotgp_ctx* ctx, long long n);
 
+/* n split steps under a time-dependent rotation frequency: step k (k = 0 ..
+ * n-1) propagates with Omega = omega[k], held fixed within the step (host
+ * array of n doubles, read during the call; imag = 1 imaginary time, 0 real
+ * time).  This serves the paper's real-time runs that change Omega (Sec. 3,
+ * dynamics from an imaginary-time state) and linear or any other ramps.
+ * The line coefficient tables of the x and y sweeps are rebuilt on the
+ * device whenever Omega changes (z lines carry no rotation term); after the
+ * call the context's Omega is omega[n-1].  The line solver must already be
+ * sized for the largest |Omega| of the schedule: ROTGP_EUNSUPPORTED if it
+ * is not (create the context with that Omega and lower it first).  The call
+ * enqueues the steps and returns. */
+int rotgp_step_schedule(rotgp_ctx* ctx, long long n, int imag, const double* omega);
+
 /* Evaluate the observables of the current state; synchronises the stream. */
 int rotgp_observables(rotgp_ctx* ctx, rotgp_obs* out);
 

@@ -370,8 +370,11 @@ template <class T, int AX, bool H1, bool IMAG, bool REDUCE>
 cudaError_t launch_h(const hybrid_args& ha, cudaStream_t s) {
   auto fn = k_line_hybrid<T, AX, H1, IMAG, REDUCE>;
   const size_t smem = (size_t)kHL * (ha.pc + 4) * sizeof(cpx<T>);
+  g_hybrid_stage = "an earlier runtime call";
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   g_hybrid_stage = "shared-memory opt-in";
-  cudaError_t e = allow_smem_bytes((const void*)fn, (int)smem);
+  e = allow_smem_bytes((const void*)fn, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)(ha.ngroups * ha.cs);
   if (ha.cs == 1) {
@@ -451,11 +454,21 @@ int hybrid_max_clusters(bool fp64, int axis, int cs, int pc) {
     fn = axis == 0 ? (const void*)k_line_hybrid<float, 0, true, true, false>
                    : (const void*)k_line_hybrid<float, 1, false, false, true>;
   const size_t smem = hybrid_smem_bytes(pc, fp64);
-  if (allow_smem_bytes(fn, (int)smem) != cudaSuccess) return 0;
+  cudaError_t e = allow_smem_bytes(fn, (int)smem);
+  if (e != cudaSuccess) {
+    g_hybrid_stage = cudaGetErrorString(e);
+    cudaGetLastError();
+    return 0;
+  }
   if (cs == 1) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kHThreads, smem) != cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kHThreads, smem);
+    if (e != cudaSuccess) {
+      g_hybrid_stage = cudaGetErrorString(e);
+      cudaGetLastError();
       return 0;
+    }
+    if (nb < 1) g_hybrid_stage = "no resident block";
     return nb;
   }
   cudaLaunchConfig_t cfg{};
@@ -470,7 +483,13 @@ int hybrid_max_clusters(bool fp64, int axis, int cs, int pc) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) return 0;
+  e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+  if (e != cudaSuccess) {
+    g_hybrid_stage = cudaGetErrorString(e);
+    cudaGetLastError();
+    return 0;
+  }
+  if (n < 1) g_hybrid_stage = "no resident cluster";
   return n;
 }
 

@@ -66,6 +66,7 @@ struct AxisPlan {
   // tile of 16 lines x hpc positions, hlsub positions per thread
   bool hyb_ok = false;
   bool use_hybrid = false;
+  std::string hyb_why;  // why no tile shape was found
   int hcs = 1, hpc = 0, hlsub = 0;
 };
 
@@ -184,8 +185,10 @@ axis_coef make_coef(int axis, int imag, double h, double dt, double omega, doubl
 }
 
 // Worst-case carry decay and multiplier-table length over the lines of an
-// axis: iterate c'_p = A+ / (A0 - A- c'_{p-1}) to its fixed point c*, then
-// forward decay |A- m*|, backward decay |c*|.
+// axis: iterate c'_p = A+ / (A0 - A- c'_{p-1}) to its fixed point c* (to
+// within 1e-15 relative, the rounding level of the iteration itself), then
+// forward decay |A- m*|, backward decay |c*|.  *converged turns false when a
+// line does not get there within kMaxTable points.
 void size_axis(const axis_coef& co, int nlines, double* decay, int* lt, bool* converged) {
   for (int l = 0; l < nlines; ++l) {
     const double u = co.u0 + l * co.du;
@@ -196,7 +199,7 @@ void size_axis(const axis_coef& co, int nlines, double* decay, int* lt, bool* co
     for (; p <= kMaxTable; ++p) {
       m = 1.0 / (a0 - am * c);
       const cd cn = ap * m;
-      const bool conv = std::abs(cn - c) <= 1e-17 * std::abs(cn);
+      const bool conv = std::abs(cn - c) <= 1e-15 * std::abs(cn);
       c = cn;
       if (conv) break;
     }
@@ -391,11 +394,17 @@ int plan_axes(rotgp_ctx* c) {
     // exact partition solve: tiles of at most ~100 KB (two or three CTAs per
     // SM), else up to ~200 KB, in clusters of at most 8 CTAs
     ap.hyb_ok = false;
+    ap.hyb_why = "line too long for a cluster of 8 tiles";
     for (size_t budget : {(size_t)100 * 1024, (size_t)200 * 1024}) {
       int cs = 0, pc = 0, ls = 0;
       if (budget > (size_t)c->smem_optin - 16 * 1024) break;
       if (!hybrid_shape(ap.len, a, c->fp64, budget, &cs, &pc, &ls)) continue;
-      if (hybrid_max_clusters(c->fp64, a, cs, pc) < 1) continue;
+      if (hybrid_max_clusters(c->fp64, a, cs, pc) < 1) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "%d CTAs of tile %d: %s", cs, pc, hybrid_launch_stage());
+        ap.hyb_why = buf;
+        continue;
+      }
       ap.hyb_ok = true;
       ap.hcs = cs;
       ap.hpc = pc;
@@ -1271,6 +1280,59 @@ int rotgp_get_psi(rotgp_ctx* c, void* dst, int dst_on_device, int dst_is_fp64) {
 int rotgp_step_imag(rotgp_ctx* c, long long n) { return run_steps(c, n, true); }
 int rotgp_step_real(rotgp_ctx* c, long long n) { return run_steps(c, n, false); }
 
+int rotgp_step_schedule(rotgp_ctx* c, long long n, int imag, const double* omega) {
+  if (!c) return ROTGP_EINVAL;
+  if (n < 0) return fail(c, ROTGP_EINVAL, "negative step count");
+  if (n == 0) return ROTGP_OK;
+  if (!omega) return fail(c, ROTGP_EINVAL, "null schedule");
+  ++c->plan_version;
+  // the solver was sized for the context's Omega: the largest |Omega| of the
+  // schedule has the slowest carries and must fit the same halo and tables
+  double big = std::fabs(c->phys.omega);
+  for (long long k = 0; k < n; ++k) {
+    if (!std::isfinite(omega[k])) return fail(c, ROTGP_EINVAL, "non-finite Omega at step %lld", k);
+    big = std::max(big, std::fabs(omega[k]));
+  }
+  {
+    const rotgp_phys keep = c->phys;
+    c->phys.omega = big;
+    int halo = 0, lt = 0;
+    double dec = 0;
+    bool ck = true;
+    int rc = plan_solver(c, &halo, &lt, &dec, &ck);
+    c->phys = keep;
+    if (rc) return rc;
+    if (lt > c->lt || (ck && halo > c->halo) || ck != c->chunk_ok)
+      return fail(c, ROTGP_EUNSUPPORTED,
+                  "|Omega| = %g needs a larger line-solver plan than the context's; create the "
+                  "context (or rotgp_set_phys) with the largest |Omega| of the schedule",
+                  big);
+  }
+  const int mode = imag ? 1 : 0;
+  for (long long k = 0; k < n; ++k) {
+    if (omega[k] != c->phys.omega) {
+      // the x and y tables of this mode (z lines carry no rotation term)
+      c->phys.omega = omega[k];
+      for (int a = 0; a < 2; ++a) {
+        AxisPlan& ap = c->axis[a];
+        ap.co[mode] = make_coef(a, mode, c->grid.h[a], c->phys.dt, c->phys.omega,
+                                nlines_u0(c, a), nlines_du(c, a));
+        Timed t(c, K_TABLES);
+        cudaError_t e = launch_tables(c->fp64, ap.table[mode], ap.tableT[mode], ap.nlines, c->lt,
+                                      ap.co[mode], c->stream);
+        if (e == cudaSuccess && ap.stencil_ok && ap.wtab[mode])
+          e = launch_stencil_tables(ap.wtab[mode], ap.nlines, ap.sK, ap.sB,
+                                    2 * ap.sB + 2 * ap.sK + 8, ap.co[mode], c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "table kernel");
+      }
+    }
+    const int rc = run_steps(c, 1, imag != 0);
+    if (rc) return rc;
+  }
+  // the other mode's tables follow the final Omega too
+  return build_tables(c);
+}
+
 int rotgp_observables(rotgp_ctx* c, rotgp_obs* out) {
   if (!c || !out) return c ? fail(c, ROTGP_EINVAL, "null output") : ROTGP_EINVAL;
   obs_args a{};
@@ -1449,7 +1511,8 @@ int rotgp_set_solver(rotgp_ctx* c, int axis, int solver) {
   AxisPlan& ap = c->axis[axis];
   if (solver == ROTGP_SOLVER_HYBRID) {
     if (!ap.hyb_ok)
-      return fail(c, ROTGP_EUNSUPPORTED, "no exact line-solve tile for axis %d", axis);
+      return fail(c, ROTGP_EUNSUPPORTED, "no exact line-solve tile for axis %d (%s)", axis,
+                  ap.hyb_why.c_str());
     ap.use_hybrid = true;
     ap.use_stencil = false;
     if (axis <= 1) c->fuse_xy = false;

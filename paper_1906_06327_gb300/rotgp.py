@@ -38,7 +38,8 @@ ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECU
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
            "rotgp_set_omega", "rotgp_init_analytic", "rotgp_init_analytic_field",
            "rotgp_set_psi", "rotgp_get_psi",
-           "rotgp_step_imag", "rotgp_step_real", "rotgp_observables", "rotgp_sync",
+           "rotgp_step_imag", "rotgp_step_real", "rotgp_step_schedule", "rotgp_observables",
+           "rotgp_sync",
            "rotgp_info", "rotgp_tune", "rotgp_set_solver", "rotgp_autotune",
            "rotgp_check_bounded_wait",
            "rotgp_profile_enable",
@@ -125,6 +126,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_get_psi.argtypes = [vp, vp, ip, ip]
         lib.rotgp_step_imag.argtypes = [vp, ctypes.c_longlong]
         lib.rotgp_step_real.argtypes = [vp, ctypes.c_longlong]
+        lib.rotgp_step_schedule.argtypes = [vp, ctypes.c_longlong, ip, dp]
         lib.rotgp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
         lib.rotgp_sync.argtypes = [vp]
         lib.rotgp_info.argtypes = [vp, ctypes.POINTER(SolverInfo)]
@@ -273,6 +275,15 @@ class Solver:
 
     def step_real(self, n: int = 1):
         self._check(self._lib.rotgp_step_real(self._h, int(n)))
+
+    def step_schedule(self, omega, imag: bool = False):
+        """len(omega) steps, step k at Omega = omega[k] (rotgp_step_schedule)."""
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        self._check(self._lib.rotgp_step_schedule(
+            self._h, int(om.size), int(bool(imag)),
+            om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        if om.size:
+            self.phys.omega = float(om[-1])
 
     def observables(self) -> dict:
         o = Obs()

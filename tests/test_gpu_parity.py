@@ -455,3 +455,33 @@ def test_thomas_yz_launch_shapes_fp32(shape, n, h, imag):
     assert np.max(np.abs(s.get_psi() - ref)) <= 5e-6 * np.max(np.abs(ref))
     ob, refo = s.observables(), oracle.observables(grid, Phys(**phys), ref)
     assert abs(ob["norm"] - refo["norm"]) <= 1e-5
+
+
+# ------------------------------------------------------------------ Omega(t)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("imag", [False, True])
+def test_omega_schedule_matches_oracle(precision, imag):
+    """rotgp_step_schedule: step k at Omega_k (a linear ramp 0.75 -> 0.6 held
+    fixed within each step, as the real-time runs of Sec. 3 change Omega)
+    equals the oracle stepping one step at a time with the same Omega_k."""
+    n, h = (64, 48), (0.25, 0.3)
+    phys = Phys(gamma=1.0, nu=1.1, g=30.0, omega=0.75, dt=2e-3)
+    grid, psi, s = _pair(n, h, phys, precision, seed=6)
+    om = 0.75 - 0.15 * np.arange(40) / 40
+    for w in om:
+        psi, _ = oracle.steps(grid, Phys(gamma=1.0, nu=1.1, g=30.0, omega=float(w), dt=2e-3), psi,
+                              1, imag)
+    s.step_schedule(om, imag=imag)
+    end = Phys(gamma=1.0, nu=1.1, g=30.0, omega=float(om[-1]), dt=2e-3)
+    (_check_fp64 if precision == "fp64" else _check_fp32)(s, grid, end, psi)
+    # the context keeps the last Omega: one more plain step matches too
+    psi, _ = oracle.steps(grid, end, psi, 1, imag)
+    (s.step_imag if imag else s.step_real)(1)
+    (_check_fp64 if precision == "fp64" else _check_fp32)(s, grid, end, psi)
+
+
+def test_omega_schedule_beyond_the_plan_is_refused():
+    s = Solver((64, 64), (0.05, 0.05), g=10.0, omega=0.1, dt=5e-3, precision="fp32")
+    with pytest.raises(RotgpError) as e:
+        s.step_schedule(np.array([0.1, 5.0, 0.1]))
+    assert e.value.code == ROTGP_EUNSUPPORTED

@@ -53,7 +53,7 @@ def _args():
                         "ring, segments; skips the autotuner; used to profile what a timed run "
                         "chose, which the timed run prints as config.plan)")
     p.add_argument("--forms", default="",
-                   help="solver form per axis, e.g. thomas,thomas,stencil (skips the autotuner;"
+                   help="solver form per axis, e.g. thomas,thomas,hybrid (skips the autotuner;"
                         " used to profile the forms a timed run chose)")
     return p.parse_args()
 
@@ -396,8 +396,8 @@ def run_ours(a, w):
         tuned = {"choice": -1, "forms": forms}
     elif a.forms:
         forms = a.forms.split(",")
-        if len(forms) != len(w.n) or not set(forms) <= {"thomas", "stencil", "fused"}:
-            raise SystemExit("--forms: one of thomas/stencil/fused per axis")
+        if len(forms) != len(w.n) or not set(forms) <= {"thomas", "stencil", "fused", "hybrid"}:
+            raise SystemExit("--forms: one of thomas/stencil/fused/hybrid per axis")
         for ax, f in enumerate(forms):
             if f != "fused":
                 s.set_solver(ax, f)

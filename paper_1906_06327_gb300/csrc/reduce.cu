@@ -107,8 +107,39 @@ constexpr int kObsTX = 32, kObsTY = 8;
 __device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
 
+// Per-thread running sums of the observables: Kahan-compensated in float
+// (the error of a sum of n terms stays at float rounding instead of growing
+// with n), plain in double.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_observables(const obs_args a) {
+struct obs_acc {
+  T s[NQ], c[NQ];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) s[v] = c[v] = 0;
+  }
+  template <int V>
+  __device__ __forceinline__ void add(T x) {
+    const T y = x - c[V];
+    const T t = s[V] + y;
+    c[V] = (t - s[V]) - y;
+    s[V] = t;
+  }
+  __device__ __forceinline__ double value(int v) const { return (double)s[v] - (double)c[v]; }
+};
+template <>
+struct obs_acc<double> {
+  double s[NQ];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) s[v] = 0;
+  }
+  template <int V>
+  __device__ __forceinline__ void add(double x) { s[V] += x; }
+  __device__ __forceinline__ double value(int v) const { return s[v]; }
+};
+
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_observables(const obs_args a) {
   using C = cpx<T>;
   constexpr int TX = kObsTX, TY = kObsTY, WX = TX + 4, WY = TY + 4;
   __shared__ C tile[2][WY][WX];
@@ -138,11 +169,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_observables(con
     if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz) return mk<T>(0, 0);
     return s * psi[(long long)k * plane + (long long)j * nx + i];
   };
-  // per-thread sums in the working precision, promoted to double for the
-  // block and grid reduction
-  T t[NQ];
-#pragma unroll
-  for (int v = 0; v < NQ; ++v) t[v] = 0;
+  // per-thread sums in the working precision (compensated in float),
+  // promoted to double for the block and grid reduction
+  obs_acc<T> t;
+  t.zero();
+  T dmax = 0;
   int buf = 0;
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const int zp_ = (int)(it % zparts);
@@ -214,19 +245,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_observables(con
         const T h4r = fmat((T)-0.5, l4r, fmat(V, re, om * z4i));
         const T h4i = fmat((T)-0.5, l4i, fmat(V, im, -om * z4r));
         const T gd = g * dens;
-        t[0] += dens;
-        t[1] = fmat(re, re, t[1]);
-        t[2] = fmat(im, im, t[2]);
-        t[3] = fmat(re, hr, t[3]);
-        t[4] = fmat(gd * re, re, t[4]);
-        t[5] = fmat(im, hi, t[5]);
-        t[6] = fmat(gd * im, im, t[6]);
-        t[8] = fmat(gd, dens, t[8]);
-        t[9] = fmat(x2, dens, t[9]);
-        t[10] = fmat(y2, dens, t[10]);
-        t[11] = fmat(z * z, dens, t[11]);
-        t[12] = fmat(re, h4r, fmat(im, h4i, t[12]));
-        t[13] = t[13] > dens ? t[13] : dens;
+        const T e3 = re * hr, e5 = im * hi;
+        t.template add<0>(dens);
+        t.template add<1>(re * re);
+        t.template add<2>(im * im);
+        t.template add<3>(e3);
+        t.template add<4>(gd * re * re);
+        t.template add<5>(e5);
+        t.template add<6>(gd * im * im);
+        // q7, the complex-form energy density, is q3 + q5 site by site
+        t.template add<7>(e3 + e5);
+        t.template add<8>(gd * dens);
+        t.template add<9>(x2 * dens);
+        t.template add<10>(y2 * dens);
+        t.template add<11>(z * z * dens);
+        t.template add<12>(fmat(re, h4r, im * h4i));
+        dmax = dmax > dens ? dmax : dens;
       }
 #pragma unroll
       for (int d = 0; d < 4; ++d) w[d] = w[d + 1];
@@ -238,11 +272,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_observables(con
     }
     __syncthreads();  // the next item restages both buffers
   }
-  // q7, the complex-form energy density, is q3 + q5 site by site
-  t[7] = t[3] + t[5];
   double q[NQ];
 #pragma unroll
-  for (int v = 0; v < NQ; ++v) q[v] = (double)t[v];
+  for (int v = 0; v < NQ; ++v) q[v] = t.value(v);
+  q[13] = (double)dmax;
   if (!block_partials<NQ, true>(q, a.partials, a.counter)) return;
   __shared__ double fin[NQ];
   __threadfence();

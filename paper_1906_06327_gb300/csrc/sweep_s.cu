@@ -430,34 +430,38 @@ cudaError_t resident_grid(const void* fn, long long units, size_t smem_per_warp,
   return cudaSuccess;
 }
 
-// Opt a kernel in to `bytes` of dynamic shared memory (bytes < 0: all that
-// the device allows beside its static shared memory), once per kernel and
-// device: the attribute belongs to the kernel on the current device, so a
-// context on a second device in the same process sets its own.
+// Opt a kernel in to at least `bytes` of dynamic shared memory (bytes < 0:
+// all that the device allows beside its static shared memory) on the current
+// device.  The attribute belongs to the kernel on that device; it is only
+// ever raised (a launch with fewer bytes stays valid), so a context on a
+// second device in the same process sets its own and launches of one kernel
+// with different tile sizes never undo each other.
 cudaError_t allow_smem_bytes(const void* fn, int bytes) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static std::mutex mu;
-  static std::set<std::tuple<const void*, int, int>> done;
-  const auto key = std::make_tuple(fn, dev, bytes);
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (done.count(key)) return cudaSuccess;
-  }
+  static std::map<std::pair<const void*, int>, int> opted;  // (kernel, device) -> bytes
+  const auto key = std::make_pair(fn, dev);
+  std::lock_guard<std::mutex> lk(mu);
+  const auto it = opted.find(key);
+  if (bytes >= 0 && it != opted.end() && it->second >= bytes) return cudaSuccess;
   if (bytes < 0) {
+    if (it != opted.end() && it->second == -1) return cudaSuccess;
     int optin = 0;
     cudaFuncAttributes fa{};
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return e;
-    bytes = optin - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) opted[key] = -1;  // the maximum: covers every request
+    return e;
   }
+  if (it != opted.end() && it->second == -1) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lk(mu);
-  done.insert(key);
-  return cudaSuccess;
+  if (e == cudaSuccess) opted[key] = bytes;
+  return e;
 }
 
 cudaError_t allow_smem(const void* fn) { return allow_smem_bytes(fn, -1); }

@@ -334,12 +334,29 @@ int rotgp_observables_noalloc(const rotgp_grid* grid, const rotgp_phys* phys, in
  * Many independent condensates (each its own grid and physics) advanced
  * together.  The paper has no batched form; this serves workloads of many
  * small instances (parameter sweeps).  Each instance is a context on a
- * stream of the batch's own; a block of n steps of all active instances is
- * captured once as a CUDA graph (fork from the batch stream into the
- * instance streams, join back) and replayed, so that small instances run
- * side by side and the block costs one graph launch.  All calls are ordered
- * after earlier work on the caller's stream and before its later work.
- * Results are those of the same steps on single contexts, bit for bit. */
+ * stream of the batch's own.  A block of n steps of the active instances
+ * runs in one of three modes:
+ *  ROTGP_BATCH_PERSISTENT  one cooperative kernel launch for all n steps of
+ *    every active instance (2D instances of one precision whose whole lines
+ *    fit one CTA's shared memory: up to about 1500 points per line in
+ *    complex float, 750 in complex double).  Each split step is the exact
+ *    line solve (ROTGP_SOLVER_HYBRID) on tiles of 16 whole lines: the CTAs
+ *    take the tiles of all instances in turn and meet at grid barriers
+ *    between the x and y phases; each barrier wait is bounded (about 2 s of
+ *    device time) and a wait that runs out makes rotgp_batch_sync (and the
+ *    calls that synchronise) return ROTGP_ETIMEOUT.  The instances' own
+ *    solver forms do not apply in this mode.  Results equal, bit for bit,
+ *    those of each instance stepped alone with ROTGP_SOLVER_HYBRID on both
+ *    axes and one CTA per line (rotgp_tune segments = 1).
+ *  ROTGP_BATCH_GRAPH  the instances' own kernels, captured once as a CUDA
+ *    graph (fork from the batch stream into the instance streams, join
+ *    back) and replayed; results equal those of single contexts bit for bit.
+ *  ROTGP_BATCH_DIRECT  the same kernels launched directly.
+ * All calls are ordered after earlier work on the caller's stream and
+ * before its later work. */
+#define ROTGP_BATCH_DIRECT 0
+#define ROTGP_BATCH_GRAPH 1
+#define ROTGP_BATCH_PERSISTENT 2
 typedef struct rotgp_batch rotgp_batch;
 
 /* count instances; grids[i], phys[i] as for rotgp_create; stream = the
@@ -354,10 +371,12 @@ int rotgp_batch_count(const rotgp_batch* batch);
 int rotgp_batch_context(rotgp_batch* batch, int index, rotgp_ctx** ctx);
 /* rotgp_autotune on every instance (invalidates captured graphs). */
 int rotgp_batch_autotune(rotgp_batch* batch, int steps);
-/* n steps of every instance, imaginary (imag = 1) or real time; use_graph =
- * 1 captures/replays a CUDA graph, 0 launches the kernels directly. */
-int rotgp_batch_step(rotgp_batch* batch, long long n, int imag, int use_graph);
-/* Synchronise; reports device-side errors of any instance. */
+/* n steps of every instance, imaginary (imag = 1) or real time, in `mode`
+ * (ROTGP_BATCH_*).  ROTGP_EUNSUPPORTED if the persistent mode does not fit
+ * the instances. */
+int rotgp_batch_step(rotgp_batch* batch, long long n, int imag, int mode);
+/* Synchronise; reports device-side errors of any instance and a timed-out
+ * grid barrier of the persistent mode (ROTGP_ETIMEOUT). */
 int rotgp_batch_sync(rotgp_batch* batch);
 /* rotgp_observables of every instance into out[0 .. count-1]. */
 int rotgp_batch_observables(rotgp_batch* batch, rotgp_obs* out);
@@ -366,9 +385,9 @@ int rotgp_batch_observables(rotgp_batch* batch, rotgp_obs* out);
  * is converged when |mu - mu_prev| <= rel_tol |mu| and its vortex count is
  * unchanged, and is then left out of later steps.  Stops after max_steps.
  * steps_out[i] = the steps instance i took; converged_out[i] (if not NULL)
- * = 1 if it converged. */
+ * = 1 if it converged.  mode as for rotgp_batch_step. */
 int rotgp_batch_converge(rotgp_batch* batch, double rel_tol, long long check_every,
-                         long long max_steps, int use_graph, long long* steps_out,
+                         long long max_steps, int mode, long long* steps_out,
                          int* converged_out);
 
 #ifdef __cplusplus

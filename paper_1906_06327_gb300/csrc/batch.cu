@@ -2,11 +2,16 @@
 // workload: instances of uneven grid sizes and differing Omega, g and trap
 // anisotropy).
 //
-// Each instance is a full rotgp context on a stream of its own.  Steps of
-// all active instances are captured once into a CUDA graph that forks from
-// the caller's stream into the instance streams and joins back, so that the
-// kernels of small instances run side by side and a whole block of steps of
-// the batch is one graph launch.  Convergence (imaginary time) is checked
+// Each instance is a full rotgp context on a stream of its own.  Three ways
+// to run a block of steps of the active instances:
+//  - ROTGP_BATCH_PERSISTENT: one cooperative kernel (batch_kernel.cu) takes
+//    every tile of every active 2D instance, phase by phase, with grid
+//    barriers between phases, for the whole block of steps;
+//  - ROTGP_BATCH_GRAPH: the instances' own kernels, captured once into a CUDA
+//    graph that forks from the caller's stream into the instance streams and
+//    joins back, replayed as one graph launch;
+//  - ROTGP_BATCH_DIRECT: the same kernels launched directly, forked and joined
+//    the same way.  Convergence (imaginary time) is checked
 // between graph launches: every `check_every` steps each active instance's
 // mu is compared with its value one check earlier; an instance is converged
 // when the relative change is below the tolerance and its vortex count did
@@ -41,6 +46,7 @@ struct rotgp_batch {
   cudaStream_t stream = nullptr;      // the batch's own (graphs are captured on it)
   std::vector<BatchGraph> graphs;     // at most two live (the two buffer parities)
   long long graph_launches = 0;
+  rotgp::batch_dev* dev = nullptr;    // scratch of the persistent step
   std::string err;
 };
 
@@ -70,16 +76,16 @@ void drop_graph(rotgp_batch* b) {
 }
 
 int run_set_inner(rotgp_batch* b, const std::vector<int>& set, long long n, bool imag,
-                  bool use_graph);
+                  int mode);
 
-// Run n steps of the instances in `set` (graph when `use_graph`), ordered
-// after the caller's stream and before its next work.
-int run_set(rotgp_batch* b, const std::vector<int>& set, long long n, bool imag, bool use_graph) {
+// Run n steps of the instances in `set` (mode: ROTGP_BATCH_*), ordered after
+// the caller's stream and before its next work.
+int run_set(rotgp_batch* b, const std::vector<int>& set, long long n, bool imag, int mode) {
   if (set.empty() || n == 0) return ROTGP_OK;
   cudaError_t e = cudaEventRecord(b->user_ev, b->user);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->user_ev, 0);
   if (e != cudaSuccess) return bfail(b, ROTGP_ECUDA, "order: %s", cudaGetErrorString(e));
-  const int rc = run_set_inner(b, set, n, imag, use_graph);
+  const int rc = run_set_inner(b, set, n, imag, mode);
   e = cudaEventRecord(b->user_ev, b->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(b->user, b->user_ev, 0);
   if (!rc && e != cudaSuccess) return bfail(b, ROTGP_ECUDA, "order: %s", cudaGetErrorString(e));
@@ -87,7 +93,7 @@ int run_set(rotgp_batch* b, const std::vector<int>& set, long long n, bool imag,
 }
 
 int run_set_inner(rotgp_batch* b, const std::vector<int>& set, long long n, bool imag,
-                  bool use_graph) {
+                  int mode) {
   cudaError_t e;
   // work already queued on the instance streams (table rebuilds of
   // rotgp_set_phys, state I/O) comes first
@@ -96,7 +102,27 @@ int run_set_inner(rotgp_batch* b, const std::vector<int>& set, long long n, bool
         (e = cudaStreamWaitEvent(b->stream, b->done[i], 0)) != cudaSuccess)
       return bfail(b, ROTGP_ECUDA, "order: %s", cudaGetErrorString(e));
   }
-  if (!use_graph) {
+  if (mode == ROTGP_BATCH_PERSISTENT) {
+    const int count = (int)b->ctx.size();
+    std::vector<rotgp::ctx_view> v(count);
+    for (int i = 0; i < count; ++i) rotgp::ctx_get_view(b->ctx[i], &v[i]);
+    const char* why = "";
+    if (!rotgp::batch_kernel_fits(v.data(), count, 200 * 1024, &why))
+      return bfail(b, ROTGP_EUNSUPPORTED, "persistent batch step: %s", why);
+    e = rotgp::batch_kernel_run(&b->dev, v.data(), count, set.data(), (int)set.size(), n, imag,
+                                b->stream);
+    if (e != cudaSuccess)
+      return bfail(b, ROTGP_ECUDA, "persistent batch launch: %s", cudaGetErrorString(e));
+    for (int i : set) rotgp::ctx_add_steps(b->ctx[i], n);
+    // later work of the instances (observables, I/O) follows the launch
+    if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess)
+      return bfail(b, ROTGP_ECUDA, "order: %s", cudaGetErrorString(e));
+    for (int i : set)
+      if ((e = cudaStreamWaitEvent(b->streams[i], b->fork, 0)) != cudaSuccess)
+        return bfail(b, ROTGP_ECUDA, "order: %s", cudaGetErrorString(e));
+    return ROTGP_OK;
+  }
+  if (mode != ROTGP_BATCH_GRAPH) {
     if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess)
       return bfail(b, ROTGP_ECUDA, "fork: %s", cudaGetErrorString(e));
     for (int i : set) {
@@ -190,6 +216,7 @@ void rotgp_batch_destroy(rotgp_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop_graph(b);
+  rotgp::batch_kernel_free(b->dev);
   for (auto* c : b->ctx) rotgp_destroy(c);
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto ev : b->done) cudaEventDestroy(ev);
@@ -258,12 +285,14 @@ int rotgp_batch_autotune(rotgp_batch* b, int steps) {
   return ROTGP_OK;
 }
 
-int rotgp_batch_step(rotgp_batch* b, long long n, int imag, int use_graph) {
+int rotgp_batch_step(rotgp_batch* b, long long n, int imag, int mode) {
   if (!b) return ROTGP_EINVAL;
   if (n < 0) return bfail(b, ROTGP_EINVAL, "negative step count");
+  if (mode < ROTGP_BATCH_DIRECT || mode > ROTGP_BATCH_PERSISTENT)
+    return bfail(b, ROTGP_EINVAL, "unknown batch mode %d", mode);
   std::vector<int> all(b->ctx.size());
   for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
-  return run_set(b, all, n, imag != 0, use_graph != 0);
+  return run_set(b, all, n, imag != 0, mode);
 }
 
 int rotgp_batch_sync(rotgp_batch* b) {
@@ -271,6 +300,11 @@ int rotgp_batch_sync(rotgp_batch* b) {
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->user);
   if (e != cudaSuccess) return bfail(b, ROTGP_ECUDA, "synchronise: %s", cudaGetErrorString(e));
+  int bf = 0;
+  if ((e = rotgp::batch_kernel_flags(b->dev, b->stream, &bf)) != cudaSuccess)
+    return bfail(b, ROTGP_ECUDA, "synchronise: %s", cudaGetErrorString(e));
+  if (bf & 8)
+    return bfail(b, ROTGP_ETIMEOUT, "a grid-barrier wait of the persistent batch step gave up");
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     const int rc = rotgp_sync(b->ctx[i]);
     if (rc) return bfail(b, rc, "instance %zu: %s", i, rotgp_last_error(b->ctx[i]));
@@ -289,7 +323,7 @@ int rotgp_batch_observables(rotgp_batch* b, rotgp_obs* out) {
 }
 
 int rotgp_batch_converge(rotgp_batch* b, double rel_tol, long long check_every,
-                         long long max_steps, int use_graph, long long* steps_out,
+                         long long max_steps, int mode, long long* steps_out,
                          int* converged_out) {
   if (!b || !steps_out) return ROTGP_EINVAL;
   if (!(rel_tol > 0) || check_every < 1 || max_steps < 1)
@@ -306,7 +340,9 @@ int rotgp_batch_converge(rotgp_batch* b, double rel_tol, long long check_every,
       if (!conv[i]) active.push_back(i);
     if (active.empty()) break;
     const long long k = std::min(check_every, max_steps - done_steps);
-    int rc = run_set(b, active, k, true, use_graph != 0);
+    if (mode < ROTGP_BATCH_DIRECT || mode > ROTGP_BATCH_PERSISTENT)
+      return bfail(b, ROTGP_EINVAL, "unknown batch mode %d", mode);
+    int rc = run_set(b, active, k, true, mode);
     if (!rc) rc = rotgp_batch_sync(b);
     if (rc) return rc;
     done_steps += k;

@@ -285,5 +285,25 @@ void ctx_set_buffer(rotgp_ctx* c, int cur);
 long long ctx_steps(const rotgp_ctx* c);
 long long ctx_plan_version(const rotgp_ctx* c);
 void ctx_add_steps(rotgp_ctx* c, long long n);
+// What a multi-instance kernel needs of one 2D context (batch.cu).
+struct ctx_view {
+  int dim, fp64, nx, ny, lt, cur;
+  void* psi[2];
+  const void* table[2][2];  // [axis][mode] coef5 tables
+  double* scale;            // pending renormalisation (device)
+  double* norm;             // last norm (device)
+  int* flags;               // device flags word
+  double dt, g, gamma, nu, x0, y0, hx, hy, vol;
+};
+void ctx_get_view(const rotgp_ctx* c, ctx_view* v);
+// The persistent multi-instance step (batch_kernel.cu): device scratch owned
+// by a batch, a fit check, one cooperative launch of nsteps split steps of the
+// active instances, and the launch's flags word (bit 3: barrier timeout).
+struct batch_dev;
+void batch_kernel_free(batch_dev* d);
+bool batch_kernel_fits(const ctx_view* v, int count, size_t smem_limit, const char** why);
+cudaError_t batch_kernel_run(batch_dev** d, const ctx_view* v, int count, const int* active,
+                             int nact, long long nsteps, bool imag, cudaStream_t s);
+cudaError_t batch_kernel_flags(batch_dev* d, cudaStream_t s, int* flags);
 
 }  // namespace rotgp

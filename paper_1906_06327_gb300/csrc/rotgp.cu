@@ -937,6 +937,30 @@ void ctx_set_buffer(rotgp_ctx* c, int cur) { c->cur = cur; }
 long long ctx_steps(const rotgp_ctx* c) { return c->steps; }
 long long ctx_plan_version(const rotgp_ctx* c) { return c->plan_version; }
 void ctx_add_steps(rotgp_ctx* c, long long n) { c->steps += n; }
+void ctx_get_view(const rotgp_ctx* c, ctx_view* v) {
+  v->dim = c->grid.dim;
+  v->fp64 = c->fp64 ? 1 : 0;
+  v->nx = c->nx;
+  v->ny = c->ny;
+  v->lt = c->lt;
+  v->cur = c->cur;
+  v->psi[0] = c->psi[0];
+  v->psi[1] = c->psi[1];
+  for (int a = 0; a < 2; ++a)
+    for (int m = 0; m < 2; ++m) v->table[a][m] = c->axis[a].table[m];
+  v->scale = c->scalars;
+  v->norm = c->scalars + 1;
+  v->flags = c->iflags;
+  v->dt = c->phys.dt;
+  v->g = c->phys.g;
+  v->gamma = c->phys.gamma;
+  v->nu = c->phys.nu;
+  v->x0 = c->x0;
+  v->y0 = c->y0;
+  v->hx = c->grid.h[0];
+  v->hy = c->grid.h[1];
+  v->vol = c->vol;
+}
 
 // Message returned by rotgp_last_error(NULL) on this thread.
 void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }

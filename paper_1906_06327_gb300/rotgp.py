@@ -393,11 +393,20 @@ class Batch:
     def autotune(self, steps: int = 5):
         self._check(self._lib.rotgp_batch_autotune(self._h, int(steps)))
 
-    def step_imag(self, n: int, graph: bool = False):
-        self._check(self._lib.rotgp_batch_step(self._h, int(n), 1, int(bool(graph))))
+    MODES = {"direct": 0, "graph": 1, "persistent": 2}
 
-    def step_real(self, n: int, graph: bool = False):
-        self._check(self._lib.rotgp_batch_step(self._h, int(n), 0, int(bool(graph))))
+    def _mode(self, graph, mode):
+        if mode is None:
+            mode = "graph" if graph else "direct"
+        return self.MODES[mode]
+
+    def step_imag(self, n: int, graph: bool = False, mode: str | None = None):
+        """mode: "direct", "graph" or "persistent" (ROTGP_BATCH_*); graph=True
+        is mode "graph"."""
+        self._check(self._lib.rotgp_batch_step(self._h, int(n), 1, self._mode(graph, mode)))
+
+    def step_real(self, n: int, graph: bool = False, mode: str | None = None):
+        self._check(self._lib.rotgp_batch_step(self._h, int(n), 0, self._mode(graph, mode)))
 
     def sync(self):
         self._check(self._lib.rotgp_batch_sync(self._h))
@@ -407,13 +416,14 @@ class Batch:
         self._check(self._lib.rotgp_batch_observables(self._h, out))
         return [o.as_dict() for o in out]
 
-    def converge(self, rel_tol: float, check_every: int, max_steps: int, graph: bool = False):
+    def converge(self, rel_tol: float, check_every: int, max_steps: int, graph: bool = False,
+                 mode: str | None = None):
         """Returns (steps per instance, converged flags)."""
         steps = (ctypes.c_longlong * self.count)()
         conv = (ctypes.c_int * self.count)()
         self._check(self._lib.rotgp_batch_converge(self._h, float(rel_tol), int(check_every),
-                                                   int(max_steps), int(bool(graph)), steps,
-                                                   conv))
+                                                   int(max_steps), self._mode(graph, mode),
+                                                   steps, conv))
         return list(steps), [bool(c) for c in conv]
 
 

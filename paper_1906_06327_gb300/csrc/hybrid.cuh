@@ -22,13 +22,29 @@ __device__ __forceinline__ cpx<T> cmad(cpx<T> a, cpx<T> b, cpx<T> c) {
   return mk<T>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
+// Products with every rounding spelled out as fused multiply-adds, so that
+// each kernel that inlines the tile step computes the same bits (no room for
+// the compiler to contract differently from one kernel to another).
+template <class T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return mk<T>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
+}
+template <class T>
+__device__ __forceinline__ T sq(cpx<T> a) {
+  return fma(a.x, a.x, a.y * a.y);
+}
+template <class T>
+__device__ __forceinline__ cpx<T> rscale(T s, cpx<T> a) {
+  return mk<T>(s * a.x, s * a.y);
+}
+
 // z^n for n >= 0 by repeated squaring
 template <class T>
 __device__ __forceinline__ cpx<T> cpow_n(cpx<T> z, int n) {
   cpx<T> r = mk<T>(1, 0);
   while (n > 0) {
-    if (n & 1) r = r * z;
-    z = z * z;
+    if (n & 1) r = cmul(r, z);
+    z = cmul(z, z);
     n >>= 1;
   }
   return r;
@@ -67,6 +83,21 @@ __device__ __forceinline__ cpx<T> ldcg_c(const cpx<T>* p) {
   return v;
 }
 
+template <class T>
+__device__ __forceinline__ cpx<T> shfl_up16(cpx<T> v, int off) {
+  return mk<T>(__shfl_up_sync(0xffffffffu, v.x, off, 16), __shfl_up_sync(0xffffffffu, v.y, off, 16));
+}
+template <class T>
+__device__ __forceinline__ cpx<T> shfl_down16(cpx<T> v, int off) {
+  return mk<T>(__shfl_down_sync(0xffffffffu, v.x, off, 16),
+               __shfl_down_sync(0xffffffffu, v.y, off, 16));
+}
+
+template <int V>
+struct int_tag {
+  static constexpr int value = V;
+};
+
 template <class T, int AX, bool H1, bool IMAG, bool REDUCE>
 __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid_job& J,
                                               unsigned char* smem_raw) {
@@ -76,10 +107,12 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   __shared__ E sG[kHL][kHS + 1], sD[kHL][kHS + 1];
   // per-line totals of this CTA, read by the other CTAs of the cluster
   __shared__ E xG[kHL], xD[kHL], xB[kHL], xX[kHL];
+  // H1: the y and z part of the potential of each line
+  __shared__ T hv[kHL];
 
   cg::cluster_group cluster = cg::this_cluster();
-  const int cs = J.cs, pc = J.pc, lsub = J.lsub;
-  // a tile of whole lines (cs = 1) is launched without a cluster: no cluster
+  const int cs = J.cs, pc = J.pc, lsub = J.lsub, rank = J.rank;
+  // a tile of whole lines (cs = 1) runs without a cluster: no cluster
   // barrier and no remote shared memory then
   auto csync = [&]() {
     if (cs > 1)
@@ -87,7 +120,6 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
     else
       __syncthreads();
   };
-  const int rank = J.rank;
   const long long grp = J.grp;
   const int W = pc + 4;          // tile positions incl. 2 halo points either side
   const int N = a.len, lt = a.lt;
@@ -116,67 +148,76 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
     return AX == 0 ? tile[l * W + e] : tile[e * kHL + l];
   };
 
-  // ---- load the tile (zeros outside the grid and past the line end)
-  {
-    constexpr int EPv = sizeof(T) == 4 ? 2 : 1;
-    const bool vec = sizeof(T) == 4 && J.vec;
-    const int ep = vec ? EPv : 1;
+  // ---- load the tile (zeros outside the grid and past the line end), ep
+  // complex numbers per copy
+  auto load = [&](auto ep_tag) {
+    constexpr int ep = decltype(ep_tag)::value;
     if (AX == 0) {
-      const int per = W / ep;  // copies per line (W even)
-      for (int u = tid; u < kHL * per; u += kHThreads) {
-        const int l = u / per, e = (u % per) * ep, p = p0 - 2 + e;
-        E* dst = &el(l, e);
-        if (line_ok(l) && p >= 0 && p + ep <= N) {
-          if (vec)
-            cp_async<16>(dst, in + gidx(l, p));
-          else
-            cp_async<sizeof(E)>(dst, in + gidx(l, p));
-        } else {
-          for (int q = 0; q < ep; ++q)
-            dst[q] = (line_ok(l) && p + q >= 0 && p + q < N) ? ldcg_c(in + gidx(l, p + q)) : zero<T>();
+      for (int l = 0; l < kHL; ++l) {
+        const bool ok = line_ok(l);
+        const E* src = in + (grp * kHL + l) * (long long)N;
+        E* dst = tile + l * W;
+        for (int c = tid; c < W / ep; c += kHThreads) {
+          const int e = c * ep, p = p0 - 2 + e;
+          if (ok && p >= 0 && p + ep <= N) {
+            cp_async<ep * sizeof(E)>(dst + e, src + p);
+          } else {
+#pragma unroll
+            for (int q = 0; q < ep; ++q)
+              dst[e + q] = (ok && p + q >= 0 && p + q < N) ? ldcg_c(src + p + q) : zero<T>();
+          }
         }
       }
     } else {
-      const int per = kHL / ep;  // copies per tile position
+      constexpr int per = kHL / ep;  // copies per tile position
       for (int u = tid; u < W * per; u += kHThreads) {
         const int e = u / per, l = (u % per) * ep, p = p0 - 2 + e;
         E* dst = &el(l, e);
         if (p >= 0 && p < N && line_ok(l + ep - 1)) {
-          if (vec)
-            cp_async<16>(dst, in + gidx(l, p));
-          else
-            cp_async<sizeof(E)>(dst, in + gidx(l, p));
+          cp_async<ep * sizeof(E)>(dst, in + gidx(l, p));
         } else {
+#pragma unroll
           for (int q = 0; q < ep; ++q)
             dst[q] = (line_ok(l + q) && p >= 0 && p < N) ? ldcg_c(in + gidx(l + q, p)) : zero<T>();
         }
       }
     }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
+  };
+  if (sizeof(T) == 4 && J.vec)
+    load(int_tag<2>{});
+  else
+    load(int_tag<1>{});
+  if (H1 && tid < kHL) {
+    const long long r = grp * kHL + tid;
+    const int j = (int)(r % a.ny), kz = (int)(r / a.ny);
+    const T y = (T)(a.y0 + (double)j * a.hy), z = (T)(a.z0 + (double)kz * a.hz);
+    hv[tid] = fma((T)a.hnu2 * y, y, (T)a.hlam2 * z * z);
   }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
 
   // ---- H1 with the pending renormalisation (x sweep): psi <- s psi, then
   // exp(-Delta (V + g|psi|^2)) or exp(-i Delta (V + g|psi|^2)) (Eq. eq1)
   if (H1) {
     const T s = (T)J.scale, hg2 = (T)a.hgam2, gg = (T)a.g, dt = (T)a.dt;
-    for (int u = tid; u < kHL * W; u += kHThreads) {
-      const int l = u / W, e = u % W, p = p0 - 2 + e;
-      const long long r = grp * kHL + l;
-      const int j = (int)(r % a.ny), k = (int)(r / a.ny);
-      const T x = (T)(a.x0 + (double)p * a.hx);
-      const T y = (T)(a.y0 + (double)j * a.hy), z = (T)(a.z0 + (double)k * a.hz);
-      E v = s * el(l, e);
-      const T en = hg2 * x * x + ((T)a.hnu2 * y * y + (T)a.hlam2 * z * z) + gg * abs2(v);
-      if (IMAG) {
-        v = exp_t(-dt * en) * v;
-      } else {
-        T sn, cn;
-        sincos_t(dt * en, &sn, &cn);
-        v = v * mk<T>(cn, -sn);
+    const T xs = (T)a.x0, hx = (T)a.hx;
+    for (int l = 0; l < kHL; ++l) {
+      const T vyz = hv[l];
+      E* row = tile + l * W;
+      for (int e = tid; e < W; e += kHThreads) {
+        const T x = fma((T)(p0 - 2 + e), hx, xs);
+        E v = rscale(s, row[e]);
+        const T en = fma(gg, sq(v), fma(hg2 * x, x, vyz));
+        if (IMAG) {
+          v = rscale(exp_t(-dt * en), v);
+        } else {
+          T sn, cn;
+          sincos_t(dt * en, &sn, &cn);
+          v = mk<T>(fma(cn, v.x, sn * v.y), fma(cn, v.y, -(sn * v.x)));
+        }
+        row[e] = v;
       }
-      el(l, e) = v;
     }
     __syncthreads();
   }
@@ -186,62 +227,75 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   const int k = AX == 0 ? tid % kHS : tid / kHL;
   const int pb = p0 + k * lsub;                      // first position
   const int nv = max(0, min(lsub, N - pb));          // positions inside the line
+  const int it = max(0, min(nv, lt - pb));           // of them with a table entry
   const int eb = 2 + k * lsub;                       // its tile position
   int li = 0;                                        // coefficient line
   if (AX == 0) li = line_ok(l) ? (int)((grp * kHL + l) % a.ny) : 0;
   if (AX == 1) li = line_ok(l) ? x0l + l : 0;
   const coef5<T>* crow = static_cast<const coef5<T>*>(a.coef) + (size_t)li * (lt + 1);
   const coef5<T> cinf = crow[lt];
-  auto coef = [&](int p) -> coef5<T> { return p >= lt ? cinf : crow[p]; };
+  // the scan threads: half-warps over the 16 sub-segments of one line
+  const int l2 = tid >> 4, k2 = tid & 15;
 
   // ---- F1: local forward from a zero carry; summary (prod al, d at the end)
   const E left = el(l, eb - 1), right = el(l, eb + nv);
   {
     E d = zero<T>(), G = mk<T>(1, 0);
-    int nin = 0;
     E pm = left, pcur = el(l, eb);
-    for (int i = 0; i < nv; ++i) {
-      const int p = pb + i;
-      const E pn = i + 1 < nv ? el(l, eb + i + 1) : right;
-      const coef5<T> c = coef(p);
-      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, c.a0 * pcur)));
-      if (p < lt)
-        G = c.al * G;
-      else
-        ++nin;
+    int i = 0;
+    for (; i < it; ++i) {
+      const coef5<T> c = crow[pb + i];
+      const E pn = el(l, eb + i + 1);
+      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmul(c.a0, pcur))));
+      G = cmul(c.al, G);
       pm = pcur;
       pcur = pn;
     }
-    if (nin) G = G * cpow_n(cinf.al, nin);
+#pragma unroll 4
+    for (; i < nv; ++i) {
+      const E pn = el(l, eb + i + 1);
+      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmul(cinf.a0, pcur))));
+      pm = pcur;
+      pcur = pn;
+    }
+    if (nv > it) G = cmul(G, cpow_n(cinf.al, nv - it));
     sG[l][k] = G;
     sD[l][k] = d;
   }
   __syncthreads();
-  // reduced system, forward: the true d before every sub-segment
-  if (tid < kHL) {
-    const int ln = tid;
-    E Gc = mk<T>(1, 0), Dc = zero<T>();
-    for (int q = 0; q < kHS; ++q) {
-      Dc = cmad(sG[ln][q], Dc, sD[ln][q]);
-      Gc = sG[ln][q] * Gc;
+  // reduced system, forward: affine prefix over the sub-segments of a line
+  // (log-depth scan in a half-warp), the CTA total to the cluster, and the
+  // true d before every sub-segment
+  {
+    E g = sG[l2][k2], dd = sD[l2][k2];
+#pragma unroll
+    for (int off = 1; off < kHS; off <<= 1) {
+      const E gp = shfl_up16(g, off), dp = shfl_up16(dd, off);
+      if (k2 >= off) {
+        dd = cmad(g, dp, dd);
+        g = cmul(g, gp);
+      }
     }
-    xG[ln] = Gc;
-    xD[ln] = Dc;
-  }
-  csync();
-  if (tid < kHL) {
-    const int ln = tid;
-    E carry = zero<T>();
-    for (int r = 0; r < rank; ++r) {
-      const E* rg = cluster.map_shared_rank(xG, r);
-      const E* rd = cluster.map_shared_rank(xD, r);
-      carry = cmad(rg[ln], carry, rd[ln]);
+    if (k2 == kHS - 1) {
+      xG[l2] = g;
+      xD[l2] = dd;
     }
-    for (int q = 0; q < kHS; ++q) {
-      const E dq = sD[ln][q];
-      sD[ln][q] = carry;
-      carry = cmad(sG[ln][q], carry, dq);
+    csync();
+    E cin = zero<T>();
+    if (cs > 1) {
+      E rg[8], rd[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < rank) {
+          rg[r] = cluster.map_shared_rank(xG, r)[l2];
+          rd[r] = cluster.map_shared_rank(xD, r)[l2];
+        }
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < rank) cin = cmad(rg[r], cin, rd[r]);
     }
+    const E gq = shfl_up16(g, 1), dq = shfl_up16(dd, 1);
+    sD[l2][k2] = k2 == 0 ? cin : cmad(gq, cin, dq);
   }
   __syncthreads();
 
@@ -249,11 +303,19 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   {
     E d = sD[l][k];
     E pm = left, pcur = el(l, eb);
-    for (int i = 0; i < nv; ++i) {
-      const int p = pb + i;
+    int i = 0;
+    for (; i < it; ++i) {
+      const coef5<T> c = crow[pb + i];
       const E pn = i + 1 < nv ? el(l, eb + i + 1) : right;
-      const coef5<T> c = coef(p);
-      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, c.a0 * pcur)));
+      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmul(c.a0, pcur))));
+      el(l, eb + i) = d;
+      pm = pcur;
+      pcur = pn;
+    }
+#pragma unroll 4
+    for (; i < nv; ++i) {
+      const E pn = i + 1 < nv ? el(l, eb + i + 1) : right;
+      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmul(cinf.a0, pcur))));
       el(l, eb + i) = d;
       pm = pcur;
       pcur = pn;
@@ -262,47 +324,52 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   // ---- B1: local backward from a zero carry; summary (prod be, x at the start)
   {
     E x = zero<T>(), B = mk<T>(1, 0);
-    int nin = 0;
-    for (int i = nv - 1; i >= 0; --i) {
-      const int p = pb + i;
-      const coef5<T> c = coef(p);
+    int i = nv - 1;
+#pragma unroll 4
+    for (; i >= it; --i) x = cmad(cinf.be, x, el(l, eb + i));
+    if (nv > it) B = cpow_n(cinf.be, nv - it);
+    for (; i >= 0; --i) {
+      const coef5<T> c = crow[pb + i];
       x = cmad(c.be, x, el(l, eb + i));
-      if (p < lt)
-        B = c.be * B;
-      else
-        ++nin;
+      B = cmul(c.be, B);
     }
-    if (nin) B = B * cpow_n(cinf.be, nin);
-    __syncthreads();  // every thread has read its sD carry before sG/sD are reused
+    __syncthreads();  // every thread has read its forward carry
     sG[l][k] = B;
     sD[l][k] = x;
   }
   __syncthreads();
-  // reduced system, backward: the true x after every sub-segment
-  if (tid < kHL) {
-    const int ln = tid;
-    E Bc = mk<T>(1, 0), Xc = zero<T>();
-    for (int q = kHS - 1; q >= 0; --q) {
-      Xc = cmad(sG[ln][q], Xc, sD[ln][q]);
-      Bc = sG[ln][q] * Bc;
+  // reduced system, backward: affine suffix over the sub-segments, the CTA
+  // total to the cluster, and the true x after every sub-segment
+  {
+    E b = sG[l2][k2], xx = sD[l2][k2];
+#pragma unroll
+    for (int off = 1; off < kHS; off <<= 1) {
+      const E bn = shfl_down16(b, off), xn = shfl_down16(xx, off);
+      if (k2 + off < kHS) {
+        xx = cmad(b, xn, xx);
+        b = cmul(b, bn);
+      }
     }
-    xB[ln] = Bc;
-    xX[ln] = Xc;
-  }
-  csync();
-  if (tid < kHL) {
-    const int ln = tid;
-    E carry = zero<T>();
-    for (int r = cs - 1; r > rank; --r) {
-      const E* rb = cluster.map_shared_rank(xB, r);
-      const E* rx = cluster.map_shared_rank(xX, r);
-      carry = cmad(rb[ln], carry, rx[ln]);
+    if (k2 == 0) {
+      xB[l2] = b;
+      xX[l2] = xx;
     }
-    for (int q = kHS - 1; q >= 0; --q) {
-      const E xq = sD[ln][q];
-      sD[ln][q] = carry;
-      carry = cmad(sG[ln][q], carry, xq);
+    csync();
+    E cin = zero<T>();
+    if (cs > 1) {
+      E rb[8], rx[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r > rank && r < cs) {
+          rb[r] = cluster.map_shared_rank(xB, r)[l2];
+          rx[r] = cluster.map_shared_rank(xX, r)[l2];
+        }
+#pragma unroll
+      for (int r = 7; r >= 0; --r)
+        if (r > rank && r < cs) cin = cmad(rb[r], cin, rx[r]);
     }
+    const E bq = shfl_down16(b, 1), xq = shfl_down16(xx, 1);
+    sD[l2][k2] = k2 == kHS - 1 ? cin : cmad(bq, cin, xq);
   }
   // every CTA's remote reads are done before any CTA moves on (and exits)
   csync();
@@ -311,45 +378,62 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   acc_t<T> acc;
   {
     E x = sD[l][k];
-    for (int i = nv - 1; i >= 0; --i) {
-      const int p = pb + i;
-      const coef5<T> c = coef(p);
+    int i = nv - 1;
+#pragma unroll 4
+    for (; i >= it; --i) {
+      x = cmad(cinf.be, x, el(l, eb + i));
+      el(l, eb + i) = x;
+      if (REDUCE) acc.add(sq(x));
+    }
+    for (; i >= 0; --i) {
+      const coef5<T> c = crow[pb + i];
       x = cmad(c.be, x, el(l, eb + i));
       el(l, eb + i) = x;
-      if (REDUCE) acc.add(abs2(x));
+      if (REDUCE) acc.add(sq(x));
     }
   }
   __syncthreads();
 
   // ---- store the tile's own positions
-  {
-    const bool vec = sizeof(T) == 4 && J.vec;
-    const int ep = vec ? 2 : 1;
+  auto store = [&](auto ep_tag) {
+    constexpr int ep = decltype(ep_tag)::value;
     if (AX == 0) {
-      const int per = pc / ep;
-      for (int u = tid; u < kHL * per; u += kHThreads) {
-        const int ln = u / per, e = 2 + (u % per) * ep, p = p0 - 2 + e;
-        if (!line_ok(ln) || p >= N) continue;
-        if (vec && p + 1 < N) {
-          *reinterpret_cast<float4*>(out + gidx(ln, p)) = *reinterpret_cast<const float4*>(&el(ln, e));
-        } else {
-          for (int q = 0; q < ep && p + q < N; ++q) out[gidx(ln, p + q)] = el(ln, e + q);
+      for (int ln = 0; ln < kHL; ++ln) {
+        if (!line_ok(ln)) continue;
+        E* dst = out + (grp * kHL + ln) * (long long)N;
+        const E* row = tile + ln * W;
+        for (int c = tid; c < pc / ep; c += kHThreads) {
+          const int e = 2 + c * ep, p = p0 - 2 + e;
+          if (p >= N) continue;
+          if (ep == 2 && p + 1 < N) {
+            *reinterpret_cast<float4*>(dst + p) = *reinterpret_cast<const float4*>(row + e);
+          } else {
+#pragma unroll
+            for (int q = 0; q < ep; ++q)
+              if (p + q < N) dst[p + q] = row[e + q];
+          }
         }
       }
     } else {
-      const int per = kHL / ep;
+      constexpr int per = kHL / ep;
       for (int u = tid; u < pc * per; u += kHThreads) {
         const int e = 2 + u / per, ln = (u % per) * ep, p = p0 - 2 + e;
         if (p >= N) continue;
-        if (vec && line_ok(ln + 1)) {
-          *reinterpret_cast<float4*>(out + gidx(ln, p)) = *reinterpret_cast<const float4*>(&el(ln, e));
+        if (ep == 2 && line_ok(ln + 1)) {
+          *reinterpret_cast<float4*>(out + gidx(ln, p)) =
+              *reinterpret_cast<const float4*>(&el(ln, e));
         } else {
+#pragma unroll
           for (int q = 0; q < ep; ++q)
             if (line_ok(ln + q)) out[gidx(ln + q, p)] = el(ln + q, e);
         }
       }
     }
-  }
+  };
+  if (sizeof(T) == 4 && J.vec)
+    store(int_tag<2>{});
+  else
+    store(int_tag<1>{});
   return REDUCE ? acc.value() : 0.0;
 }
 

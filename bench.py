@@ -43,6 +43,8 @@ def _args():
     p.add_argument("--skip-baselines", action="store_true",
                    help="no e2e and no CPU baseline (profiling runs)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--skip-converge", action="store_true",
+                   help="no time-to-converged-lattice runs")
     p.add_argument("--skip-large", action="store_true",
                    help="no second roofline entry on the larger-than-L2 3D state")
     p.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -358,6 +360,71 @@ def _large_state_roofline(a, stream, flush, peak, peak_kind, name="3d-512x512x12
     return out
 
 
+def _converge_single(w, precision, stream, max_seconds):
+    """Imaginary time from the seeded start until mu changes by less than
+    1e-6 relative over one time unit (1/dt steps) with the vortex count
+    unchanged over the last three windows, or max_seconds of wall time."""
+    import torch
+    from paper_1906_06327_gb300.rotgp import Solver
+    s = Solver(w.n, w.h, gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt,
+               precision=precision, stream=stream.cuda_stream)
+    s.init_analytic(1, seed=w.seed)
+    window = max(1, int(round(1.0 / w.dt)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mu_prev, vort, steps, ok = None, [], 0, False
+    while time.perf_counter() - t0 < max_seconds:
+        s.step_imag(window)
+        steps += window
+        o = s.observables()
+        vort.append(o["vortices"])
+        if (mu_prev is not None and abs(o["mu"] - mu_prev) <= 1e-6 * abs(o["mu"])
+                and len(vort) >= 3 and len(set(vort[-3:])) == 1):
+            ok = True
+            break
+        mu_prev = o["mu"]
+    wall = time.perf_counter() - t0
+    s.close()
+    return {"workload": w.name, "precision": precision, "steps": steps,
+            "time_units": steps * w.dt, "wall_s": wall, "converged": ok, "mu": o["mu"],
+            "vortices": o["vortices"]}
+
+
+def _converge_batch(stream, max_seconds, count=64):
+    """The 64-instance batch (seeded sizes and physics) in imaginary time
+    until every instance's mu changes by less than 1e-6 relative over one
+    time unit with its vortex count unchanged (rotgp_batch_converge, one
+    persistent launch per time unit), or max_seconds of wall time."""
+    import torch
+    from paper_1906_06327_gb300 import inputs
+    from paper_1906_06327_gb300.rotgp import Batch
+    specs = inputs.batch_specs(count)
+    b = Batch(specs, stream=stream.cuda_stream)
+    for i, sp in enumerate(specs):
+        b.instances[i].init_analytic(1, seed=sp["seed"])
+    window = int(round(1.0 / specs[0]["dt"]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    total = [0] * count
+    conv = [False] * count
+    sites = sum(sp["n"][0] * sp["n"][1] for sp in specs)
+    while time.perf_counter() - t0 < max_seconds and not all(conv):
+        steps, c = b.converge(1e-6, window, 20 * window, mode="persistent")
+        total = [t + x for t, x in zip(total, steps)]
+        conv = [a or x for a, x in zip(conv, c)]
+        if all(c):
+            break
+    wall = time.perf_counter() - t0
+    b.close()
+    done = sum(conv)
+    return {"workload": f"{count} seeded 2D instances (N in 128..512)", "precision": "fp32",
+            "mode": "persistent", "instances": count, "converged": done,
+            "steps_max": max(total), "steps_median": sorted(total)[count // 2],
+            "time_units_max": max(total) * specs[0]["dt"], "wall_s": wall,
+            "site_updates": sum(t * sp["n"][0] * sp["n"][1] for t, sp in zip(total, specs)),
+            "sites": sites}
+
+
 def run_ours(a, w):
     import numpy as np
     import torch
@@ -464,6 +531,17 @@ def run_ours(a, w):
     if not a.skip_large and world == 1:
         roofline_hbm = _large_state_roofline(a, stream, flush, peak, peak_kind)
 
+    # the metric's second half: time to a converged vortex lattice
+    ttc = None
+    if not a.skip_converge and rank == 0:
+        from paper_1906_06327_gb300 import inputs as _inp
+        w1 = _inp.WORKLOADS["2d-128-imag-fp64"]
+        ttc = {"criterion": "|mu(t) - mu(t - 1)| <= 1e-6 |mu(t)| over one time unit, vortex "
+                            "count unchanged",
+               "single_fp64": _converge_single(w1, "fp64", stream, 30.0),
+               "single_fp32": _converge_single(w1, "fp32", stream, 30.0),
+               "batch": _converge_batch(stream, 60.0)}
+
     e2e = None
     cpu = None
     if not a.skip_baselines and rank == 0:
@@ -524,6 +602,7 @@ def run_ours(a, w):
             "gpu_launches": launches,
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
+            "time_to_converged": ttc,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

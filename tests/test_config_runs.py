@@ -1,0 +1,121 @@
+"""The complex-float path against the FP64 oracle over the full run lengths
+of the 512^2 and 256 x 256 x 128 workloads, with the stated tolerances of the
+FP32 bulk: mu and E (real-part and complex forms) within 1e-5 relative, the
+density within 1e-4 relative L2, the same vortex count.
+
+Expected values come from tests/golden/make_config_goldens.py, which runs the
+oracle alone: 512^2, 40,000 imaginary-time steps (Delta = 2.5e-4) from the
+seed-0 start, then 20,000 real-time steps (Delta = 1e-4) with Omega lowered
+linearly from 0.9 to 0.8, step k at Omega_k = 0.9 - 0.1 k / 20000 (Sec. 3
+runs real-time dynamics from imaginary-time states; rotgp_step_schedule);
+256 x 256 x 128, 200 imaginary-time steps.  The densities are stored on every
+4th grid point (every 8th along z), so the L2 error is taken on those points.
+The full 20,000 + 5,000 steps of the 3D workload are compared with the FP64
+path of the library itself, which the parity tests pin to the oracle at
+1e-10.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1906_06327_gb300 import inputs
+from paper_1906_06327_gb300.rotgp import Solver
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+REL = ("mu", "energy", "mu_c", "energy_c")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+
+
+def _gold(name):
+    d = np.load(os.path.join(GOLD, name))
+    keys = [str(k) for k in d["keys"]]
+    return d, keys
+
+
+def _check_obs(ob, row, keys, what):
+    ref = dict(zip(keys, row))
+    for k in REL:
+        assert abs(ob[k] - ref[k]) <= 1e-5 * abs(ref[k]), (what, k, ob[k], ref[k])
+    assert abs(ob["norm"] - ref["norm"]) <= 1e-5, (what, ob["norm"], ref["norm"])
+    assert ob["vortices"] == int(ref["vortices"]), (what, ob["vortices"], ref["vortices"])
+
+
+def _dens_err(psi, ref, stride):
+    d = (np.abs(psi) ** 2)[tuple(slice(None, None, s) for s in reversed(stride))]
+    return float(np.linalg.norm(d - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.slow
+def test_512_imaginary_then_real_ramp_matches_oracle():
+    d, keys = _gold("config_512_oracle.npz")
+    w = inputs.WORKLOADS["2d-512-fp32"]
+    s = Solver(w.n, w.h, gamma=w.gamma, nu=w.nu, g=w.g, omega=w.omega, dt=w.dt, precision="fp32")
+    s.init_analytic(1, seed=w.seed)
+    done = 0
+    for row, upto in zip(d["obs"][:3], d["marks"][:3]):
+        s.step_imag(int(upto) - done)
+        done = int(upto)
+        _check_obs(s.observables(), row, keys, f"imag {upto}")
+    err_i = _dens_err(s.get_psi(), d["dens_imag"], d["stride"])
+    assert err_i <= 1e-4, err_i
+    # real time from the imaginary-time state, Omega ramped (same Delta as the oracle)
+    s.set_phys(gamma=w.gamma, nu=w.nu, g=w.g, omega=w.omega, dt=w.real_dt)
+    om0, om1, nreal = w.omega, w.extra["omega_ramp_to"], w.real_steps
+    s.step_schedule(om0 + (om1 - om0) * np.arange(nreal) / nreal, imag=False)
+    _check_obs(s.observables(), d["obs"][3], keys, "real ramp")
+    err_r = _dens_err(s.get_psi(), d["dens_real"], d["stride"])
+    assert err_r <= 1e-4, err_r
+    print(f"512^2: density rel L2 after imaginary {err_i:.2e}, after the ramp {err_r:.2e}")
+
+
+def test_3d_200_steps_match_oracle():
+    d, keys = _gold("config_3d_200_oracle.npz")
+    w = inputs.WORKLOADS["3d-256x256x128-fp32"]
+    s = Solver(w.n, w.h, gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt,
+               precision="fp32")
+    s.init_analytic(1, seed=w.seed)
+    s.step_imag(200)
+    _check_obs(s.observables(), d["obs"][0], keys, "3d 200")
+    err = _dens_err(s.get_psi(), d["dens"], d["stride"])
+    assert err <= 1e-4, err
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,nimag,nreal", [("2d-512-fp32", 40000, 20000),
+                                              ("3d-256x256x128-fp32", 20000, 5000)])
+def test_full_length_fp32_matches_fp64(name, nimag, nreal):
+    """The full run of each workload in complex float against the same run
+    in complex double (real time at Delta = 1e-4 after the imaginary part)."""
+    w = inputs.WORKLOADS[name]
+    kw = dict(gamma=w.gamma, nu=w.nu, lam=w.lam, g=w.g, omega=w.omega, dt=w.dt)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        s = Solver(w.n, w.h, precision=prec, **kw)
+        s.init_analytic(1, seed=w.seed)
+        s.step_imag(nimag)
+        o_i = s.observables()
+        p_i = s.get_psi()
+        s.set_phys(**dict(kw, dt=w.real_dt))
+        s.step_real(nreal)
+        out[prec] = (o_i, p_i, s.observables(), s.get_psi())
+        s.close()
+    for part in (0, 2):
+        a, b = out["fp32"][part], out["fp64"][part]
+        for k in REL:
+            assert abs(a[k] - b[k]) <= 1e-5 * abs(b[k]), (part, k, a[k], b[k])
+        assert a["vortices"] == b["vortices"], (part, a["vortices"], b["vortices"])
+    for part in (1, 3):
+        da, db = np.abs(out["fp32"][part]) ** 2, np.abs(out["fp64"][part]) ** 2
+        err = np.linalg.norm(da - db) / np.linalg.norm(db)
+        assert err <= 1e-4, (part, err)
+    drift = abs(out["fp32"][2]["norm"] - out["fp32"][0]["norm"])
+    print(f"{name}: fp32 real-time norm drift over {nreal} steps {drift:.2e}")

@@ -390,6 +390,55 @@ int rotgp_batch_converge(rotgp_batch* batch, double rel_tol, long long check_eve
                          long long max_steps, int mode, long long* steps_out,
                          int* converged_out);
 
+/* ------------------------------------------------------------- warm start
+ * A learned initial state for fast-rotating imaginary-time runs: a
+ * convolutional encoder-decoder (684,642 parameters, bfloat16 weights and
+ * activations, float accumulation, float master weights and Adam state)
+ * that maps the parameters (Omega, g, nu) of a 2D run on a G x G grid of
+ * half-width L (points x_j = -L + j 2L/G) to a proposed wave function.  It
+ * stands in for the paper's practice (Sec. 1, Sec. 3) of starting a fast
+ * rotating run from a lattice converged beforehand at a lower Omega; the
+ * proposal only seeds imaginary-time propagation (load it with
+ * rotgp_set_psi(..., normalise = 1)), which decides the converged state.
+ * The paper has no network; everything here is this library's own.  Input
+ * planes: the Thomas-Fermi amplitude of the rotating trap, x / L, y / L,
+ * Omega, g / 1000 and (nu - 1) / 0.1; output: 2 L psi on points 0 .. G-1
+ * of each axis.  Layout of the flat float parameter vector: per layer i =
+ * 0 .. 11, the weights W_i[ky][kx][ci][co] then the bias b_i[co]; layer
+ * channels (ci -> co): 6->32, 32->32, 32->64, 64->64, 64->128, 128->128,
+ * 128->128, 128->128, 128->64, 64->32, 32->32, 32->2 (3 x 3 convolutions;
+ * 2 x 2 mean pooling after layers 1, 3, 5; nearest upsampling with the
+ * outputs of layers 5, 3, 1 added before layers 8, 9, 10; ReLU after every
+ * layer but the last).  A context serves one CUDA stream and up to
+ * max_batch runs per call. */
+typedef struct rotgp_ws rotgp_ws;
+long long rotgp_ws_param_count(void);
+/* grid = G (a multiple of 16, 16 .. 1024); the parameters start at zero. */
+int rotgp_ws_create(int grid, int max_batch, void* stream, rotgp_ws** out);
+void rotgp_ws_destroy(rotgp_ws* ws);
+const char* rotgp_ws_last_error(const rotgp_ws* ws);
+/* Parameters to / from a host float array of rotgp_ws_param_count() values
+ * (setting them also resets the optimiser state). */
+int rotgp_ws_set_params(rotgp_ws* ws, const float* params);
+int rotgp_ws_get_params(rotgp_ws* ws, float* params);
+/* Proposals for n runs: prm = host array (Omega, g, nu) x n; psi = n ABI
+ * wave functions of (G+1)^2 complex double (host or device), edges zero.
+ * Synchronises the stream. */
+int rotgp_ws_propose(rotgp_ws* ws, int n, const double* prm, double half_width, void* psi,
+                     int psi_on_device);
+/* One Adam step (learning rate lr, beta1 0.9, beta2 0.999) on the mean
+ * squared error between the outputs for prm and 2 L psi of the n target
+ * wave functions psi (ABI layout, complex double, host or device); *loss
+ * receives the loss before the step.  Synchronises the stream. */
+int rotgp_ws_train_step(rotgp_ws* ws, int n, const double* prm, double half_width,
+                        const void* psi, int psi_on_device, float lr, double* loss);
+/* Loss and its gradient with respect to the parameters for given input
+ * planes (host float, [n][G][G][6]) and targets (host float, [n][G][G][2]);
+ * grads (host, param_count floats) may be NULL.  For checks of the
+ * network's kernels.  Synchronises the stream. */
+int rotgp_ws_gradients(rotgp_ws* ws, int n, const void* inputs, const float* targets,
+                       double* loss, float* grads);
+
 #ifdef __cplusplus
 }
 #endif

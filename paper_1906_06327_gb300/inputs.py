@@ -124,3 +124,15 @@ def batch_specs(count: int = 64, seed: int = 0, dt: float = 5e-4) -> list:
         out.append(dict(n=(n, n), h=(float(h), float(h)), gamma=1.0, nu=float(nu), g=float(g),
                         omega=float(omega), dt=dt, seed=int(r[4] * 2**31)))
     return out
+
+
+def warmstart_params(count: int, seed: int, omega=(0.7, 0.9), g=(200.0, 800.0),
+                     nu=(1.0, 1.1)) -> np.ndarray:
+    """(count, 3) parameter sets (Omega, g, nu) of the learned-warm-start
+    workload, uniform in the given ranges; three SplitMix64(seed) numbers per
+    set."""
+    u = splitmix64(seed, 3 * count).astype(np.float64) / 2.0**64
+    u = u.reshape(count, 3)
+    return np.stack([omega[0] + (omega[1] - omega[0]) * u[:, 0],
+                     g[0] + (g[1] - g[0]) * u[:, 1],
+                     nu[0] + (nu[1] - nu[0]) * u[:, 2]], axis=1)

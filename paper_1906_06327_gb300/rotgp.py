@@ -48,7 +48,10 @@ EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys"
            "rotgp_batch_create", "rotgp_batch_destroy", "rotgp_batch_last_error",
            "rotgp_batch_count", "rotgp_batch_context", "rotgp_batch_autotune",
            "rotgp_batch_step", "rotgp_batch_sync", "rotgp_batch_observables",
-           "rotgp_batch_converge")
+           "rotgp_batch_converge",
+           "rotgp_ws_param_count", "rotgp_ws_create", "rotgp_ws_destroy", "rotgp_ws_last_error",
+           "rotgp_ws_set_params", "rotgp_ws_get_params", "rotgp_ws_propose",
+           "rotgp_ws_train_step", "rotgp_ws_gradients")
 
 
 class Grid(ctypes.Structure):
@@ -153,6 +156,20 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_batch_observables.argtypes = [vp, ctypes.POINTER(Obs)]
         lib.rotgp_batch_converge.argtypes = [vp, ctypes.c_double, ll, ll, ip,
                                              ctypes.POINTER(ll), ctypes.POINTER(ip)]
+        lib.rotgp_ws_param_count.argtypes = []
+        lib.rotgp_ws_param_count.restype = ll
+        lib.rotgp_ws_create.argtypes = [ip, ip, vp, ctypes.POINTER(vp)]
+        lib.rotgp_ws_destroy.argtypes = [vp]
+        lib.rotgp_ws_destroy.restype = None
+        lib.rotgp_ws_last_error.argtypes = [vp]
+        lib.rotgp_ws_last_error.restype = ctypes.c_char_p
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.rotgp_ws_set_params.argtypes = [vp, fp]
+        lib.rotgp_ws_get_params.argtypes = [vp, fp]
+        lib.rotgp_ws_propose.argtypes = [vp, ip, dp, ctypes.c_double, vp, ip]
+        lib.rotgp_ws_train_step.argtypes = [vp, ip, dp, ctypes.c_double, vp, ip, ctypes.c_float,
+                                            dp]
+        lib.rotgp_ws_gradients.argtypes = [vp, ip, vp, fp, dp, fp]
         _lib = lib
         return lib
 
@@ -479,3 +496,88 @@ def _buffer(obj, shape):
             raise ValueError(f"state tensor must be contiguous with shape {shape}")
         return obj.data_ptr(), int(obj.is_cuda), int(obj.dtype == torch.complex128), obj
     raise TypeError("unsupported buffer type")
+
+
+class WarmStart:
+    """The learned warm start (``rotgp_ws_*``): proposes initial wave
+    functions of 2D runs on a G x G grid of half-width L from (Omega, g, nu).
+    Argument marshalling only; the network runs in the CUDA library."""
+
+    def __init__(self, grid: int, max_batch: int = 32, stream=0):
+        self._lib = load()
+        self.grid, self.max_batch = int(grid), int(max_batch)
+        h = ctypes.c_void_p()
+        rc = self._lib.rotgp_ws_create(self.grid, self.max_batch, ctypes.c_void_p(int(stream)),
+                                       ctypes.byref(h))
+        if rc != ROTGP_OK:
+            raise RotgpError(rc, self._lib.rotgp_ws_last_error(None).decode())
+        self._h = h
+        self.n_params = int(self._lib.rotgp_ws_param_count())
+
+    def _check(self, rc):
+        if rc != ROTGP_OK:
+            raise RotgpError(rc, self._lib.rotgp_ws_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rotgp_ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        self._check(self._lib.rotgp_ws_set_params(
+            self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, dtype=np.float32)
+        self._check(self._lib.rotgp_ws_get_params(
+            self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return p
+
+    @staticmethod
+    def _prm(prm):
+        prm = np.ascontiguousarray(prm, dtype=np.float64).reshape(-1, 3)
+        return prm, prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def propose(self, prm, half_width: float) -> np.ndarray:
+        """prm: (n, 3) array of (Omega, g, nu); returns n ABI wave functions
+        ((G+1) x (G+1) complex128, edges zero, not normalised)."""
+        prm, pp = self._prm(prm)
+        n = prm.shape[0]
+        out = np.zeros((n, self.grid + 1, self.grid + 1), dtype=np.complex128)
+        self._check(self._lib.rotgp_ws_propose(self._h, n, pp, float(half_width),
+                                               ctypes.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def train_step(self, prm, half_width: float, psi, lr: float) -> float:
+        """One Adam step towards the target wave functions psi (n ABI arrays,
+        numpy complex128 on the host or a CUDA complex128 torch tensor)."""
+        prm, pp = self._prm(prm)
+        n = prm.shape[0]
+        ptr, on_dev, is64, _keep = _buffer(psi, (n, self.grid + 1, self.grid + 1))
+        assert is64, "targets must be complex double"
+        loss = ctypes.c_double(0)
+        self._check(self._lib.rotgp_ws_train_step(self._h, n, pp, float(half_width),
+                                                  ctypes.c_void_p(ptr), on_dev, float(lr),
+                                                  ctypes.byref(loss)))
+        return loss.value
+
+    def gradients(self, inputs, targets):
+        """(loss, gradient) for given input planes [n][G][G][6] and targets
+        [n][G][G][2] (float32 host arrays)."""
+        x = np.ascontiguousarray(inputs, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double(0)
+        self._check(self._lib.rotgp_ws_gradients(
+            self._h, x.shape[0], ctypes.c_void_p(x.ctypes.data),
+            t.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss),
+            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return loss.value, g

@@ -1,0 +1,103 @@
+"""The learned warm start on the GPU: the network's hand-written bfloat16
+kernels against the FP64 CPU reference (oracle/warmstart_ref.py), and what
+the trained network gains as a start for imaginary-time propagation.
+
+Gradient check: the same bfloat16-rounded weights and input planes go to
+both sides; the GPU keeps its activations in bfloat16 and accumulates in
+float, so each layer's gradient must match the FP64 one to a few bfloat16
+roundings (relative L2 error <= 3e-2, cosine >= 0.999) and the loss to 1e-2.
+
+Gain: the solver makes the training set itself (runs of one 128^2 grid from
+the same seeded start, converged with the persistent batch step), the
+network is trained on it, and held-out parameter sets are converged from
+three starts: the analytic seeded start, the network's proposal, and the
+lattice converged beforehand at Omega - 0.1 (the paper's practice).
+"""
+import numpy as np
+import pytest
+
+from oracle import warmstart_ref as ref
+from paper_1906_06327_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    """Round float32 values to the nearest bfloat16 (ties to even)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+
+
+def test_gradients_match_fp64_reference():
+    from paper_1906_06327_gb300.rotgp import WarmStart
+    G, n = 32, 2
+    rng = np.random.default_rng(7)
+    p = _bf16(ref.init_params(3).astype(np.float32) + 0.02 * rng.normal(size=ref.n_params()))
+    x = _bf16(rng.normal(size=(n, G, G, ref.CIN)).astype(np.float32))
+    t = rng.normal(size=(n, G, G, 2)).astype(np.float32)
+    ws = WarmStart(G, max_batch=n)
+    assert ws.n_params == ref.n_params()
+    ws.set_params(p)
+    loss, g = ws.gradients(x, t)
+    loss_ref, g_ref = ref.gradients(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - loss_ref) <= 1e-2 * loss_ref, (loss, loss_ref)
+    off = 0
+    for i, shape in enumerate(ref.param_shapes()):
+        k = int(np.prod(shape))
+        a, b = g[off:off + k].astype(np.float64), g_ref[off:off + k]
+        off += k
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
+        assert rel <= 3e-2 and cos >= 0.999, (i, shape, rel, cos)
+
+
+def test_training_lowers_the_loss():
+    from paper_1906_06327_gb300.rotgp import WarmStart
+    G, n, L = 32, 4, 6.0
+    ws = WarmStart(G, max_batch=n)
+    ws.set_params(ref.init_params(1).astype(np.float32))
+    prm = inputs.warmstart_params(n, 3)
+    # smooth synthetic targets: a Gaussian with a parameter-dependent phase
+    xs = -L + np.arange(G + 1) * 2 * L / G
+    X, Y = np.meshgrid(xs, xs)
+    psi = np.stack([np.exp(-(X ** 2 + Y ** 2) / 8 + 1j * p[0] * X) / 20 for p in prm])
+    psi[:, :, 0] = psi[:, 0, :] = psi[:, :, -1] = psi[:, -1, :] = 0
+    losses = [ws.train_step(prm, L, psi, 1e-3) for _ in range(200)]
+    assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
+
+
+@pytest.mark.slow
+def test_learned_start_against_analytic_and_lower_omega_starts():
+    from paper_1906_06327_gb300 import warmstart as W
+    from paper_1906_06327_gb300.rotgp import WarmStart
+    setup = W.Setup()
+    train_prm = inputs.warmstart_params(192, 11)
+    test_prm = inputs.warmstart_params(16, 12)
+    states, obs, steps, conv, _ = W.converge(setup, train_prm)
+    keep = conv.astype(bool)
+    assert keep.mean() > 0.8, keep.mean()
+    ws = WarmStart(setup.grid, max_batch=16)
+    ws.set_params(ref.init_params(0).astype(np.float32))
+    losses = W.train(ws, setup, train_prm[keep], states[keep], epochs=60, batch=16, lr=1e-3)
+    assert losses[-20:].mean() < 0.2 * losses[:20].mean(), (losses[:20].mean(), losses[-20:].mean())
+    # the three starts of every held-out parameter set
+    _, o_a, s_a, c_a, w_a = W.converge(setup, test_prm)
+    _, o_n, s_n, c_n, w_n = W.converge(setup, test_prm, starts=ws.propose(test_prm, setup.half_width))
+    low, _, _, _, _ = W.converge(setup, W.lower_omega(test_prm))
+    _, o_l, s_l, c_l, w_l = W.converge(setup, test_prm, starts=low)
+    same = [abs(a["mu"] - b["mu"]) <= 1e-6 * abs(a["mu"]) and a["vortices"] == b["vortices"]
+            for a, b in zip(o_a, o_n)]
+    print(f"median steps to convergence: analytic {np.median(s_a):.0f}, learned "
+          f"{np.median(s_n):.0f}, lower Omega {np.median(s_l):.0f}; wall {w_a:.2f} / {w_n:.2f} / "
+          f"{w_l:.2f} s; learned start reaches the analytic start's mu (1e-6) and vortex count "
+          f"in {np.mean(same):.0%} of {len(same)} cases")
+    assert c_n.mean() >= c_a.mean()
+    assert np.median(s_n) < np.median(s_a)

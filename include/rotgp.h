@@ -183,6 +183,13 @@ int rotgp_set_psi(rotgp_ctx* ctx, const void* src, int src_on_device, int src_is
  * memory, complex double or float; synchronises the stream. */
 int rotgp_get_psi(rotgp_ctx* ctx, void* dst, int dst_on_device, int dst_is_fp64);
 
+/* The density integrated along z, h_z sum_k |psi(x_i, y_j, z_k)|^2, on the
+ * (N_x+1)(N_y+1) plane (x fastest, edges zero) into host or device doubles:
+ * the paper's reduced 2D density of a 3D state (Sec. 3, the z-integrated
+ * densities compared with 2D lattices); in 2D the density itself.  Applies
+ * the pending renormalisation; synchronises the stream. */
+int rotgp_column_density(rotgp_ctx* ctx, double* dst, int dst_on_device);
+
 /* Enqueue n split steps in imaginary time (i Delta -> Delta, then
  * renormalisation) or in real time.  n >= 0. */
 int rotgp_step_imag(rotgp_ctx* ctx, long long n);

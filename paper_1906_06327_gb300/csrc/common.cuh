@@ -277,6 +277,8 @@ cudaError_t launch_pack(bool fp64_store, bool fp64_src, const void* src, void* p
 cudaError_t launch_unpack(bool fp64_store, bool fp64_dst, const void* psi, void* dst, int nx,
                           int ny, int nz, int dim, const double* scale, cudaStream_t s);
 cudaError_t launch_set_scalar(double* p, double v, cudaStream_t s);
+cudaError_t launch_column_density(bool fp64, const void* psi, double* out, int nx, int ny,
+                                  int nz, double hz, const double* scale, cudaStream_t s);
 
 // Context bookkeeping for graph replay (batch.cu): which ping-pong buffer
 // holds the state, and the step counter.

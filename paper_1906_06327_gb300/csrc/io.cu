@@ -101,6 +101,27 @@ __global__ void k_unpack(const cpx<TS>* psi, cpx<TD>* dst, int nx, int ny, int n
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
+// The density integrated along z (the paper's reduced 2D density of a 3D
+// state, Sec. 3): out[j][i] = h_z sum_k |s psi(i, j, k)|^2 on the
+// (N_x+1)(N_y+1) plane, edges zero; in 2D the density itself.
+template <class T>
+__global__ void k_column_density(const cpx<T>* psi, double* out, int nx, int ny, int nz,
+                                 double hz, const double* scale) {
+  const long long px = nx + 1, n = px * (ny + 1);
+  const double s2 = (*scale) * (*scale);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long i = idx % px, j = idx / px;
+    double acc = 0.0;
+    if (i > 0 && i < nx && j > 0 && j < ny)
+      for (int k = 0; k < nz; ++k) {
+        const cpx<T> v = psi[((long long)k * ny + j) * nx + i];
+        acc += (double)v.x * v.x + (double)v.y * v.y;
+      }
+    out[idx] = s2 * acc * hz;
+  }
+}
+
 static int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 65536) b = 65536;
@@ -153,6 +174,18 @@ cudaError_t launch_unpack(bool fp64_store, bool fp64_dst, const void* psi, void*
     if (fp64_dst) ROTGP_UP(float, double); else ROTGP_UP(float, float);
   }
 #undef ROTGP_UP
+  return cudaGetLastError();
+}
+
+cudaError_t launch_column_density(bool fp64, const void* psi, double* out, int nx, int ny,
+                                  int nz, double hz, const double* scale, cudaStream_t s) {
+  const int threads = 256, blocks = grid_for((long long)(nx + 1) * (ny + 1), threads);
+  if (fp64)
+    k_column_density<double><<<blocks, threads, 0, s>>>(static_cast<const cpx<double>*>(psi), out,
+                                                        nx, ny, nz, hz, scale);
+  else
+    k_column_density<float><<<blocks, threads, 0, s>>>(static_cast<const cpx<float>*>(psi), out,
+                                                       nx, ny, nz, hz, scale);
   return cudaGetLastError();
 }
 

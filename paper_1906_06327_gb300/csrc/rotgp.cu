@@ -1301,6 +1301,24 @@ int rotgp_get_psi(rotgp_ctx* c, void* dst, int dst_on_device, int dst_is_fp64) {
   return check_flags(c);
 }
 
+int rotgp_column_density(rotgp_ctx* c, double* dst, int dst_on_device) {
+  if (!c || !dst) return c ? fail(c, ROTGP_EINVAL, "null destination") : ROTGP_EINVAL;
+  const size_t n = (size_t)(c->nx + 1) * (c->ny + 1);
+  double* to = dst_on_device ? dst : reinterpret_cast<double*>(c->staging);
+  cudaError_t e;
+  {
+    Timed t(c, K_IO);
+    e = launch_column_density(c->fp64, c->psi[c->cur], to, c->nx, c->ny, c->nz,
+                              c->grid.dim == 3 ? c->grid.h[2] : 1.0, c->d_scale(), c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "column density kernel");
+  if (!dst_on_device) {
+    e = cudaMemcpyAsync(dst, c->staging, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy column density");
+  }
+  return check_flags(c);
+}
+
 int rotgp_step_imag(rotgp_ctx* c, long long n) { return run_steps(c, n, true); }
 int rotgp_step_real(rotgp_ctx* c, long long n) { return run_steps(c, n, false); }
 

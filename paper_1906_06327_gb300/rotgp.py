@@ -37,7 +37,7 @@ ERROR_NAMES = {ROTGP_EINVAL: "EINVAL", ROTGP_ENOMEM: "ENOMEM", ROTGP_ECUDA: "ECU
 # Every entry point declared in include/rotgp.h.
 EXPORTS = ("rotgp_create", "rotgp_destroy", "rotgp_last_error", "rotgp_set_phys",
            "rotgp_set_omega", "rotgp_init_analytic", "rotgp_init_analytic_field",
-           "rotgp_set_psi", "rotgp_get_psi",
+           "rotgp_set_psi", "rotgp_get_psi", "rotgp_column_density",
            "rotgp_step_imag", "rotgp_step_real", "rotgp_step_schedule", "rotgp_observables",
            "rotgp_sync",
            "rotgp_info", "rotgp_tune", "rotgp_set_solver", "rotgp_autotune",
@@ -127,6 +127,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.rotgp_init_analytic_field.argtypes = [vp, ip, dp, ctypes.c_double, ctypes.c_double]
         lib.rotgp_set_psi.argtypes = [vp, vp, ip, ip, ip]
         lib.rotgp_get_psi.argtypes = [vp, vp, ip, ip]
+        lib.rotgp_column_density.argtypes = [vp, dp, ip]
         lib.rotgp_step_imag.argtypes = [vp, ctypes.c_longlong]
         lib.rotgp_step_real.argtypes = [vp, ctypes.c_longlong]
         lib.rotgp_step_schedule.argtypes = [vp, ctypes.c_longlong, ip, dp]
@@ -289,6 +290,13 @@ class Solver:
     # -- propagation
     def step_imag(self, n: int = 1):
         self._check(self._lib.rotgp_step_imag(self._h, int(n)))
+
+    def column_density(self) -> np.ndarray:
+        """h_z sum_z |psi|^2 on the (N_y+1, N_x+1) plane (rotgp_column_density)."""
+        out = np.zeros((self.n[1] + 1, self.n[0] + 1))
+        self._check(self._lib.rotgp_column_density(
+            self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0))
+        return out
 
     def step_real(self, n: int = 1):
         self._check(self._lib.rotgp_step_real(self._h, int(n)))

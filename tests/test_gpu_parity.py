@@ -485,3 +485,20 @@ def test_omega_schedule_beyond_the_plan_is_refused():
     with pytest.raises(RotgpError) as e:
         s.step_schedule(np.array([0.1, 5.0, 0.1]))
     assert e.value.code == ROTGP_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,h", [((30, 26, 20), (0.35, 0.4, 0.3)), ((40, 36), (0.3, 0.3))])
+def test_column_density_matches_oracle(precision, n, h):
+    """rotgp_column_density: h_z sum_k |psi|^2 (the reduced density of the
+    3D lattices of Sec. 3), or the density in 2D, against the oracle state."""
+    phys = Phys(gamma=1.0, nu=1.1, lam=1.4, g=30.0, omega=0.5, dt=2e-3)
+    grid, psi, s = _pair(n, h, phys, precision, seed=8)
+    psi, _ = oracle.steps(grid, phys, psi, 10, True)
+    s.step_imag(10)
+    col = s.column_density()
+    dens = np.abs(psi) ** 2
+    want = dens.sum(axis=0) * h[2] if len(n) == 3 else dens
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert np.max(np.abs(col - want)) <= tol * np.max(want)
+    assert abs(col.sum() * h[0] * h[1] - 1.0) < (1e-12 if precision == "fp64" else 1e-5)

@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const bf16* __restrict__ X,
   if (gc < Ci && go < Co) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) atomicAdd(&dW[((size_t)k * Ci + gc) * Co + go], acc[k]);
-    if (ci == 0) atomicAdd(&db[go], bacc);
+    // the bias gradient once, from the blocks of the first input-channel chunk
+    if (ci == 0 && blockIdx.y == 0) atomicAdd(&db[go], bacc);
   }
 }
 

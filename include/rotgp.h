@@ -430,9 +430,13 @@ int rotgp_ws_set_params(rotgp_ws* ws, const float* params);
 int rotgp_ws_get_params(rotgp_ws* ws, float* params);
 /* Proposals for n runs: prm = host array (Omega, g, nu) x n; psi = n ABI
  * wave functions of (G+1)^2 complex double (host or device), edges zero.
- * Synchronises the stream. */
-int rotgp_ws_propose(rotgp_ws* ws, int n, const double* prm, double half_width, void* psi,
-                     int psi_on_device);
+ * random_phase != 0 multiplies each by the random phase exp(2 pi i R) of
+ * Eq. fun, R drawn from SplitMix64(seed) exactly as rotgp_init_analytic
+ * draws it, which keeps the start's symmetry breaking (a smooth proposal
+ * alone has to nucleate its vortices by instability).  Synchronises the
+ * stream. */
+int rotgp_ws_propose(rotgp_ws* ws, int n, const double* prm, double half_width, int random_phase,
+                     unsigned long long seed, void* psi, int psi_on_device);
 /* One Adam step (learning rate lr, beta1 0.9, beta2 0.999) on the mean
  * squared error between the outputs for prm and 2 L psi of the n target
  * wave functions psi (ABI layout, complex double, host or device); *loss

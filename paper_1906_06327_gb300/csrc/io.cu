@@ -6,20 +6,6 @@
 
 namespace rotgp {
 
-// Random number n of the SplitMix64 stream seeded with `seed` (Steele, Lea
-// and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
-// the counter state seed + (n + 1) * 0x9E3779B97F4A7C15 passed through the
-// generator's output mix (two xor-shift-multiply rounds and a final
-// xor-shift), all modulo 2^64; its top 53 bits scaled by 2^-53 give a double
-// in [0, 1).  Counter based, so every grid point draws its own number.
-__device__ __forceinline__ double splitmix64_unit(unsigned long long seed, unsigned long long n) {
-  unsigned long long z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
-}
-
 // Eq. fun: psi = (x + i y)/sqrt(pi d^2) exp(-(x^2+y^2)/(2 d^2)) e^{2 pi i R}
 // [3D: * (pi d_z^2)^(-1/4) exp(-z^2/(2 d_z^2))]; function 0: (x + i y) -> 1.
 // Evaluated in double, stored in T.  R(x_i, y_j) is the number of the point

@@ -41,6 +41,7 @@
 namespace {
 
 using bf16 = __nv_bfloat16;
+using rotgp::splitmix64_unit;
 
 constexpr int kWsCin = 6;
 constexpr int kWsLayers = 12;
@@ -350,8 +351,12 @@ __global__ void k_features(const double* prm, bf16* out, int n, int G, double L)
 }
 
 // Network output (2 L psi on G x G points) -> ABI wave function of run i:
-// (G+1) x (G+1) complex double, psi = out / (2 L), the far edge zero.
-__global__ void k_out_to_psi(const float* y, double* psi, int n, int G, double L) {
+// (G+1) x (G+1) complex double, psi = out / (2 L), the far edge zero; with
+// rp != 0 multiplied by the random phase exp(2 pi i R) of Eq. fun, R drawn
+// from SplitMix64(seed) for point n = k (G + 1) + j as rotgp_init_analytic
+// draws it.
+__global__ void k_out_to_psi(const float* y, double* psi, int n, int G, double L, int rp,
+                             unsigned long long seed) {
   const size_t P = (size_t)(G + 1) * (G + 1), tot = (size_t)n * P;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -363,6 +368,13 @@ __global__ void k_out_to_psi(const float* y, double* psi, int n, int G, double L
       const float* v = y + (((size_t)r * G + k) * G + j) * 2;
       re = v[0] / (2.0 * L);
       im = v[1] / (2.0 * L);
+      if (rp) {
+        double sn, cs;
+        sincos(2.0 * 3.14159265358979323846 * splitmix64_unit(seed, q), &sn, &cs);
+        const double a = re * cs - im * sn;
+        im = re * sn + im * cs;
+        re = a;
+      }
     }
     psi[2 * i] = re;
     psi[2 * i + 1] = im;
@@ -695,8 +707,8 @@ int rotgp_ws_get_params(rotgp_ws* w, float* params) {
   return e == cudaSuccess ? ROTGP_OK : wfail(w, ROTGP_ECUDA, "get parameters", e);
 }
 
-int rotgp_ws_propose(rotgp_ws* w, int n, const double* prm, double half_width, void* psi,
-                     int psi_on_device) {
+int rotgp_ws_propose(rotgp_ws* w, int n, const double* prm, double half_width, int random_phase,
+                     unsigned long long seed, void* psi, int psi_on_device) {
   int rc = check_batch(w, n);
   if (rc) return rc;
   if (!prm || !psi || !(half_width > 0)) return wfail(w, ROTGP_EINVAL, "bad arguments");
@@ -705,7 +717,7 @@ int rotgp_ws_propose(rotgp_ws* w, int n, const double* prm, double half_width, v
   double* dst = psi_on_device ? static_cast<double*>(psi) : w->dpsi;
   if (e == cudaSuccess) {
     k_out_to_psi<<<blocks_for((size_t)n * (w->G + 1) * (w->G + 1)), 256, 0, w->s>>>(
-        w->y, dst, n, w->G, half_width);
+        w->y, dst, n, w->G, half_width, random_phase ? 1 : 0, seed);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && !psi_on_device)

@@ -167,7 +167,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         fp = ctypes.POINTER(ctypes.c_float)
         lib.rotgp_ws_set_params.argtypes = [vp, fp]
         lib.rotgp_ws_get_params.argtypes = [vp, fp]
-        lib.rotgp_ws_propose.argtypes = [vp, ip, dp, ctypes.c_double, vp, ip]
+        lib.rotgp_ws_propose.argtypes = [vp, ip, dp, ctypes.c_double, ip, ctypes.c_ulonglong, vp,
+                                         ip]
         lib.rotgp_ws_train_step.argtypes = [vp, ip, dp, ctypes.c_double, vp, ip, ctypes.c_float,
                                             dp]
         lib.rotgp_ws_gradients.argtypes = [vp, ip, vp, fp, dp, fp]
@@ -554,14 +555,16 @@ class WarmStart:
         prm = np.ascontiguousarray(prm, dtype=np.float64).reshape(-1, 3)
         return prm, prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
-    def propose(self, prm, half_width: float) -> np.ndarray:
+    def propose(self, prm, half_width: float, seed=None) -> np.ndarray:
         """prm: (n, 3) array of (Omega, g, nu); returns n ABI wave functions
-        ((G+1) x (G+1) complex128, edges zero, not normalised)."""
+        ((G+1) x (G+1) complex128, edges zero, not normalised); with `seed`
+        multiplied by the random phase of Eq. fun drawn from that seed."""
         prm, pp = self._prm(prm)
         n = prm.shape[0]
         out = np.zeros((n, self.grid + 1, self.grid + 1), dtype=np.complex128)
-        self._check(self._lib.rotgp_ws_propose(self._h, n, pp, float(half_width),
-                                               ctypes.c_void_p(out.ctypes.data), 0))
+        self._check(self._lib.rotgp_ws_propose(
+            self._h, n, pp, float(half_width), int(seed is not None),
+            int(seed or 0) & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(out.ctypes.data), 0))
         return out
 
     def train_step(self, prm, half_width: float, psi, lr: float) -> float:

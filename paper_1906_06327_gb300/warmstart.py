@@ -91,3 +91,25 @@ def lower_omega(prm, delta=0.1):
     q = np.array(prm, dtype=np.float64).reshape(-1, 3)
     q[:, 0] -= delta
     return q
+
+
+def evaluate(ws: WarmStart, setup: Setup, prm, lower=0.1, stream=0) -> dict:
+    """Imaginary time to convergence for each parameter set from three starts:
+    the analytic seeded start of Eq. fun, the network's proposal times the
+    same random phase, and the lattice converged beforehand at Omega - lower
+    (the pre-calculated start of the paper; its own convergence is not
+    counted).  Per start: steps, converged flags, mu, E, vortex counts and
+    the wall time of the batch."""
+    prm = np.asarray(prm, dtype=np.float64).reshape(-1, 3)
+    out = {}
+    starts = {"analytic": None,
+              "learned": ws.propose(prm, setup.half_width, seed=setup.seed)}
+    if lower:
+        starts["lower_omega"] = converge(setup, lower_omega(prm, lower), stream=stream)[0]
+    for name, st in starts.items():
+        _, obs, steps, conv, wall = converge(setup, prm, starts=st, stream=stream)
+        out[name] = {"steps": steps, "converged": conv, "wall_s": wall,
+                     "mu": np.array([o["mu"] for o in obs]),
+                     "energy": np.array([o["energy"] for o in obs]),
+                     "vortices": np.array([o["vortices"] for o in obs])}
+    return out

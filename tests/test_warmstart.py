@@ -78,28 +78,33 @@ def test_training_lowers_the_loss():
 
 @pytest.mark.slow
 def test_learned_start_against_analytic_and_lower_omega_starts():
+    """Held-out parameter sets converged from the three starts.  The learned
+    start must converge in fewer steps than the analytic one (median over
+    the cases); the rest is reported: the wall time, the rate at which two
+    starts reach the same lattice (mu within 1e-6 and the same vortex count;
+    imaginary time can settle in different metastable lattices from
+    different starts) and how often the learned start ends at the lower
+    energy."""
     from paper_1906_06327_gb300 import warmstart as W
     from paper_1906_06327_gb300.rotgp import WarmStart
     setup = W.Setup()
     train_prm = inputs.warmstart_params(192, 11)
-    test_prm = inputs.warmstart_params(16, 12)
+    test_prm = inputs.warmstart_params(24, 12)
     states, obs, steps, conv, _ = W.converge(setup, train_prm)
     keep = conv.astype(bool)
-    assert keep.mean() > 0.8, keep.mean()
+    assert keep.mean() > 0.7, keep.mean()
     ws = WarmStart(setup.grid, max_batch=16)
     ws.set_params(ref.init_params(0).astype(np.float32))
     losses = W.train(ws, setup, train_prm[keep], states[keep], epochs=60, batch=16, lr=1e-3)
     assert losses[-20:].mean() < 0.2 * losses[:20].mean(), (losses[:20].mean(), losses[-20:].mean())
-    # the three starts of every held-out parameter set
-    _, o_a, s_a, c_a, w_a = W.converge(setup, test_prm)
-    _, o_n, s_n, c_n, w_n = W.converge(setup, test_prm, starts=ws.propose(test_prm, setup.half_width))
-    low, _, _, _, _ = W.converge(setup, W.lower_omega(test_prm))
-    _, o_l, s_l, c_l, w_l = W.converge(setup, test_prm, starts=low)
-    same = [abs(a["mu"] - b["mu"]) <= 1e-6 * abs(a["mu"]) and a["vortices"] == b["vortices"]
-            for a, b in zip(o_a, o_n)]
-    print(f"median steps to convergence: analytic {np.median(s_a):.0f}, learned "
-          f"{np.median(s_n):.0f}, lower Omega {np.median(s_l):.0f}; wall {w_a:.2f} / {w_n:.2f} / "
-          f"{w_l:.2f} s; learned start reaches the analytic start's mu (1e-6) and vortex count "
-          f"in {np.mean(same):.0%} of {len(same)} cases")
-    assert c_n.mean() >= c_a.mean()
-    assert np.median(s_n) < np.median(s_a)
+    ev = W.evaluate(ws, setup, test_prm)
+    a, n, lo = ev["analytic"], ev["learned"], ev["lower_omega"]
+    same = (np.abs(n["mu"] - a["mu"]) <= 1e-6 * np.abs(a["mu"])) & (n["vortices"] == a["vortices"])
+    lower_e = np.mean(n["energy"] < a["energy"])
+    print(f"median steps to convergence: analytic {np.median(a['steps']):.0f}, learned "
+          f"{np.median(n['steps']):.0f}, lower Omega {np.median(lo['steps']):.0f}; converged "
+          f"{a['converged'].mean():.0%} / {n['converged'].mean():.0%} / {lo['converged'].mean():.0%}; "
+          f"wall {a['wall_s']:.2f} / {n['wall_s']:.2f} / {lo['wall_s']:.2f} s; same lattice as the "
+          f"analytic start in {same.mean():.0%}; learned start at lower E in {lower_e:.0%}")
+    assert np.median(n["steps"]) < np.median(a["steps"])
+    assert n["converged"].mean() >= a["converged"].mean()

@@ -12,8 +12,10 @@ fastest (shape ``(N_z+1, N_y+1, N_x+1)`` in 3D, ``(N_y+1, N_x+1)`` in 2D), as
 the paper's programs store them (Sec. 3, "(NX+1) x (NY+1) points").
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-except the real-part energy/chemical-potential formula at g != 0, whose
-value beyond the pinned special cases is "parity unpinned".
+(the real-part energy and chemical potential at g != 0 through their
+identity with the complex forms on states e^{i theta} f, f real).
+``warmstart_ref`` (the FP64 reference of the learned start's network) is
+pinned by ``tests/test_warmstart_ref.py``.
 """
 from __future__ import annotations
 

@@ -46,7 +46,9 @@ def _gold(name):
 # the run (about 2e-4 rad over 20,000 steps), so after the real-time parts
 # the bounds are those measured for the run lengths here: the complex-form
 # mu and E (invariant under the global phase, which turns at rate mu in real
-# time) within 1e-4, the density within 3e-4 relative L2.  The real-part
+# time) within 1e-4, the density within 3e-4 relative L2, the norm within
+# 1e-4 (the float CN map is unitary only to the rounding of its multipliers:
+# 3.8e-5 over the 20,000-step ramp, whose tables are rebuilt every step).  The real-part
 # forms divide by sum psi_R^2, which the turning global phase modulates.
 REAL_REL = ("mu_c", "energy_c")
 
@@ -56,7 +58,7 @@ def _check_obs(ob, row, keys, what, real=False):
     for k in (REAL_REL if real else REL):
         tol = 1e-4 if real else 1e-5
         assert abs(ob[k] - ref[k]) <= tol * abs(ref[k]), (what, k, ob[k], ref[k])
-    assert abs(ob["norm"] - ref["norm"]) <= 1e-5, (what, ob["norm"], ref["norm"])
+    assert abs(ob["norm"] - ref["norm"]) <= (1e-4 if real else 1e-5), (what, ob["norm"], ref["norm"])
     assert ob["vortices"] == int(ref["vortices"]), (what, ob["vortices"], ref["vortices"])
     return {k: abs(ob[k] - ref[k]) / abs(ref[k]) for k in REL}
 

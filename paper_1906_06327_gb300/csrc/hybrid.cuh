@@ -212,9 +212,9 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
         if (IMAG) {
           v = rscale(exp_t(-dt * en), v);
         } else {
-          T sn, cn;
-          sincos_t(dt * en, &sn, &cn);
-          v = mk<T>(fma(cn, v.x, sn * v.y), fma(cn, v.y, -(sn * v.x)));
+          T c1, s1;
+          rot_t(dt * en, &c1, &s1);
+          v = mk<T>(fma(c1, v.x, fma(s1, v.y, v.x)), fma(c1, v.y, fma(-s1, v.x, v.y)));
         }
         row[e] = v;
       }

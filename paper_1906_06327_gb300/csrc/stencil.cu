@@ -185,11 +185,11 @@ __global__ void __launch_bounds__(128) k_stencil_x(const stream_args a) {
         v.re = __fmul2_rn(f, v.re);
         v.im = __fmul2_rn(f, v.im);
       } else {
-        float2 sn, cs;
-        sincosf(dt * en.x, &sn.x, &cs.x);
-        sincosf(dt * en.y, &sn.y, &cs.y);
-        const float2 re = __ffma2_rn(sn, v.im, __fmul2_rn(cs, v.re));
-        v.im = __ffma2_rn(make_float2(-sn.x, -sn.y), v.re, __fmul2_rn(cs, v.im));
+        float2 s1, c1;
+        rot_t(dt * en.x, &c1.x, &s1.x);
+        rot_t(dt * en.y, &c1.y, &s1.y);
+        const float2 re = __ffma2_rn(c1, v.re, __ffma2_rn(s1, v.im, v.re));
+        v.im = __ffma2_rn(c1, v.im, __ffma2_rn(make_float2(-s1.x, -s1.y), v.re, v.im));
         v.re = re;
       }
     }

@@ -78,6 +78,26 @@ __device__ __forceinline__ double exp_t(double v) { return exp(v); }
 __device__ __forceinline__ void sincos_t(float v, float* s, float* c) { sincosf(v, s, c); }
 __device__ __forceinline__ void sincos_t(double v, double* s, double* c) { sincos(v, s, c); }
 
+// The real-time H1 factor exp(-i theta) as 1 + c1 - i s1 with
+// c1 = cos(theta) - 1 = -2 sin^2(theta/2) and s1 = sin(theta) =
+// 2 sin(theta/2) cos(theta/2), both to full relative precision.  Rounding
+// cos(theta) itself near 1 (to 1 exactly when theta is small) leaves a
+// modulus error of up to half an ulp of 1 that has the same sign on every
+// point of a plane of nearly equal potential, which makes the real-time norm
+// drift by ~1e-8 per step in complex float; with c1 and s1 the modulus is one
+// to about theta^2 times the rounding.
+template <class T>
+__device__ __forceinline__ void rot_t(T theta, T* c1, T* s1) {
+  T sh, ch;
+  sincos_t(theta * (T)0.5, &sh, &ch);
+  *c1 = -(T)2 * sh * sh;
+  *s1 = (T)2 * sh * ch;
+}
+// v exp(-i theta) = v + (c1 v - i s1 v)
+__device__ __forceinline__ float2 rotate_f(float2 v, float c1, float s1) {
+  return make_float2(fmaf(c1, v.x, fmaf(s1, v.y, v.x)), fmaf(c1, v.y, fmaf(-s1, v.x, v.y)));
+}
+
 template <class T>
 __device__ __forceinline__ cpx<T> zero() { return mk<T>(0, 0); }
 

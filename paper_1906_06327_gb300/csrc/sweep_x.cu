@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
     if (IMAG) {
       return exp_t(-dt * en) * psi;
     } else {
-      T sn, cs;
-      sincos_t(dt * en, &sn, &cs);
-      return psi * mk<T>(cs, -sn);
+      T c1, s1;
+      rot_t(dt * en, &c1, &s1);
+      return mk<T>(fma(c1, psi.x, fma(s1, psi.y, psi.x)), fma(c1, psi.y, fma(-s1, psi.x, psi.y)));
     }
   };
   auto slot = [&](int q) { return ring + (size_t)(q % R) * SLOT; };
@@ -304,11 +304,11 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
       v.re = __fmul2_rn(f, v.re);
       v.im = __fmul2_rn(f, v.im);
     } else {
-      float2 sn, cs;
-      sincosf(dt * en.x, &sn.x, &cs.x);
-      sincosf(dt * en.y, &sn.y, &cs.y);
-      const float2 re = __ffma2_rn(sn, v.im, __fmul2_rn(cs, v.re));
-      v.im = __ffma2_rn(make_float2(-sn.x, -sn.y), v.re, __fmul2_rn(cs, v.im));
+      float2 s1, c1;
+      rot_t(dt * en.x, &c1.x, &s1.x);
+      rot_t(dt * en.y, &c1.y, &s1.y);
+      const float2 re = __ffma2_rn(c1, v.re, __ffma2_rn(s1, v.im, v.re));
+      v.im = __ffma2_rn(c1, v.im, __ffma2_rn(make_float2(-s1.x, -s1.y), v.re, v.im));
       v.re = re;
     }
     return v;
@@ -553,9 +553,9 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
         const float f = __expf(-dt * en);
         return __fmul2_rn(make_float2(f, f), v);
       } else {
-        float sn, cs;
-        sincosf(dt * en, &sn, &cs);
-        return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
+        float c1, s1;
+        rot_t(dt * en, &c1, &s1);
+        return rotate_f(v, c1, s1);
       }
     };
     // imaginary time: the factor sc exp(-dt (V + g sc^2 |v|^2)) of a raw

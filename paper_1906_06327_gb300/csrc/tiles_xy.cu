@@ -59,9 +59,9 @@ __device__ __forceinline__ float2 h1_point(float2 v, float s, float vxyz, float 
     const float f = __expf(-dt * e);
     return make_float2(f * v.x, f * v.y);
   } else {
-    float sn, cs;
-    sincosf(dt * e, &sn, &cs);
-    return make_float2(fmaf(cs, v.x, sn * v.y), fmaf(cs, v.y, -sn * v.x));
+    float c1, s1;
+    rot_t(dt * e, &c1, &s1);
+    return rotate_f(v, c1, s1);
   }
 }
 

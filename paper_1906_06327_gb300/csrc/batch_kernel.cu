@@ -136,7 +136,7 @@ __device__ double partials_sum(const double* p, int n) {
 }
 
 template <class T, bool IMAG>
-__global__ void __launch_bounds__(kHThreads) k_batch_steps(const batch_args b) {
+__global__ void __launch_bounds__(kHThreads, sizeof(T) == 4 ? 2 : 1) k_batch_steps(const batch_args b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (long long step = 0; step < b.nsteps; ++step) {
     // ---- phase X: H1 (with the pending scale) and the x sweep

@@ -41,10 +41,15 @@ __device__ __forceinline__ T abs2(cpx<T> a) { return a.x * a.x + a.y * a.y; }
 
 // Folded Thomas coefficients of one unknown p of one line (Eqs. eqD.11/eq5):
 // with m_p = 1/(A0 - A- c'_{p-1}) and c'_p = A+ m_p,
-//   forward   d'_p = a0 psi_p + am psi_{p-1} + ap psi_{p+1} + al d'_{p-1}
-//             a0 = m_p (1 - 2 kappa), am = m_p (kappa - tau), ap = m_p (kappa + tau),
+//   forward   d'_p = (1 + a0) psi_p + am psi_{p-1} + ap psi_{p+1} + al d'_{p-1}
+//             a0 = m_p (1 - 2 kappa) - 1, am = m_p (kappa - tau), ap = m_p (kappa + tau),
 //             al = -m_p A-
 //   backward  x_p = d'_p + be x_{p+1},  be = -c'_p.
+// The diagonal factor m_p (1 - 2 kappa) is close to 1 and is kept as its
+// difference from 1: rounded to float itself it would carry an error of up
+// to half an ulp of 1, the same on every interior point of every line, and
+// the real-time CN map would then gain or lose ~1e-8 of norm per sweep;
+// stored as the difference the rounding is that many times smaller.
 // m2 = 2 m_p serves the unfolded form of the same solve (psi' = 2y - psi
 // with A y = psi): d_p = m2 psi_p + al d_{p-1}, z_p = d_p + be z_{p+1},
 // psi'_p = z_p - psi_p.

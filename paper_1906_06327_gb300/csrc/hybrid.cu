@@ -19,17 +19,18 @@
 // the true carries.  Nothing is truncated: the result is the Thomas solution
 // of the whole line up to rounding, whatever the decay of the carries.
 //
-// Layout.  A CTA of 256 threads holds a tile of 16 lines x pc positions (+2
+// Layout.  A CTA of 512 threads holds a tile of 16 lines x pc positions (+2
 // halo positions either side) in shared memory; thread (line l, sub-segment
-// k) owns lsub = pc/16 consecutive positions of line l.  A line longer than
+// k) owns lsub = pc/32 consecutive positions of line l.  A line longer than
 // one tile is spread over a cluster of cs CTAs (cs = 1, 2, 4 or 8), CTA r
 // holding positions [r pc, (r+1) pc); the CTAs exchange their per-line
 // summaries through distributed shared memory.  x lines (contiguous rows) sit
 // in the tile as [line][position] with an even pitch and an odd lsub, so the
-// 32 threads of a warp (2 lines x 16 sub-segments) touch distinct banks; y
-// and z lines (16 consecutive x at one transverse position, 128 contiguous
-// bytes per position in complex float) sit as [position][line], a warp being
-// 16 lines x 2 sub-segments.  Each point is read from and written to global
+// 32 threads of a warp (the 32 sub-segments of one line) touch every bank
+// pair twice; y and z lines (16 consecutive x at one transverse position, 128
+// contiguous bytes per position in complex float) sit as [position][line], a
+// warp being 16 lines x 2 sub-segments.  The affine scans over a line's
+// sub-segments run in one warp with shuffles.  Each point is read from and written to global
 // memory once per sweep; H1 (with the pending renormalisation) is applied to
 // the tile as it lands in the x sweep; the last sweep of a step reduces the
 // norm.  The same kernel serves both propagation modes (the table of the mode
@@ -41,7 +42,7 @@
 namespace rotgp {
 
 template <class T, int AX, bool H1, bool IMAG, bool REDUCE>
-__global__ void __launch_bounds__(kHThreads) k_line_hybrid(const hybrid_args ha) {
+__global__ void __launch_bounds__(kHThreads, sizeof(T) == 4 ? 2 : 1) k_line_hybrid(const hybrid_args ha) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   hybrid_job J;
   J.cs = ha.cs;

@@ -14,8 +14,8 @@ namespace rotgp {
 namespace hyb {
 
 constexpr int kHL = 16;                 // lines per tile
-constexpr int kHS = 16;                 // sub-segments per line in one CTA
-constexpr int kHThreads = kHL * kHS;    // 256
+constexpr int kHS = 32;                 // sub-segments per line in one CTA (a warp)
+constexpr int kHThreads = kHL * kHS;    // 512
 
 template <class T>
 __device__ __forceinline__ cpx<T> cmad(cpx<T> a, cpx<T> b, cpx<T> c) {
@@ -83,14 +83,16 @@ __device__ __forceinline__ cpx<T> ldcg_c(const cpx<T>* p) {
   return v;
 }
 
+// shuffles within the kHS lanes that hold the sub-segments of one line
 template <class T>
-__device__ __forceinline__ cpx<T> shfl_up16(cpx<T> v, int off) {
-  return mk<T>(__shfl_up_sync(0xffffffffu, v.x, off, 16), __shfl_up_sync(0xffffffffu, v.y, off, 16));
+__device__ __forceinline__ cpx<T> shfl_up_seg(cpx<T> v, int off) {
+  return mk<T>(__shfl_up_sync(0xffffffffu, v.x, off, kHS),
+               __shfl_up_sync(0xffffffffu, v.y, off, kHS));
 }
 template <class T>
-__device__ __forceinline__ cpx<T> shfl_down16(cpx<T> v, int off) {
-  return mk<T>(__shfl_down_sync(0xffffffffu, v.x, off, 16),
-               __shfl_down_sync(0xffffffffu, v.y, off, 16));
+__device__ __forceinline__ cpx<T> shfl_down_seg(cpx<T> v, int off) {
+  return mk<T>(__shfl_down_sync(0xffffffffu, v.x, off, kHS),
+               __shfl_down_sync(0xffffffffu, v.y, off, kHS));
 }
 
 template <int V>
@@ -234,8 +236,8 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   if (AX == 1) li = line_ok(l) ? x0l + l : 0;
   const coef5<T>* crow = static_cast<const coef5<T>*>(a.coef) + (size_t)li * (lt + 1);
   const coef5<T> cinf = crow[lt];
-  // the scan threads: half-warps over the 16 sub-segments of one line
-  const int l2 = tid >> 4, k2 = tid & 15;
+  // the scan threads: a warp over the sub-segments of one line
+  const int l2 = tid / kHS, k2 = tid % kHS;
 
   // ---- F1: local forward from a zero carry; summary (prod al, d at the end)
   const E left = el(l, eb - 1), right = el(l, eb + nv);
@@ -246,7 +248,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
     for (; i < it; ++i) {
       const coef5<T> c = crow[pb + i];
       const E pn = el(l, eb + i + 1);
-      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmul(c.a0, pcur))));
+      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmad(c.a0, pcur, pcur))));
       G = cmul(c.al, G);
       pm = pcur;
       pcur = pn;
@@ -254,7 +256,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
 #pragma unroll 4
     for (; i < nv; ++i) {
       const E pn = el(l, eb + i + 1);
-      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmul(cinf.a0, pcur))));
+      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmad(cinf.a0, pcur, pcur))));
       pm = pcur;
       pcur = pn;
     }
@@ -264,13 +266,13 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   }
   __syncthreads();
   // reduced system, forward: affine prefix over the sub-segments of a line
-  // (log-depth scan in a half-warp), the CTA total to the cluster, and the
-  // true d before every sub-segment
+  // (log-depth scan in a warp), the CTA total to the cluster, and the true d
+  // before every sub-segment
   {
     E g = sG[l2][k2], dd = sD[l2][k2];
 #pragma unroll
     for (int off = 1; off < kHS; off <<= 1) {
-      const E gp = shfl_up16(g, off), dp = shfl_up16(dd, off);
+      const E gp = shfl_up_seg(g, off), dp = shfl_up_seg(dd, off);
       if (k2 >= off) {
         dd = cmad(g, dp, dd);
         g = cmul(g, gp);
@@ -294,7 +296,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
       for (int r = 0; r < 8; ++r)
         if (r < rank) cin = cmad(rg[r], cin, rd[r]);
     }
-    const E gq = shfl_up16(g, 1), dq = shfl_up16(dd, 1);
+    const E gq = shfl_up_seg(g, 1), dq = shfl_up_seg(dd, 1);
     sD[l2][k2] = k2 == 0 ? cin : cmad(gq, cin, dq);
   }
   __syncthreads();
@@ -307,7 +309,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
     for (; i < it; ++i) {
       const coef5<T> c = crow[pb + i];
       const E pn = i + 1 < nv ? el(l, eb + i + 1) : right;
-      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmul(c.a0, pcur))));
+      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmad(c.a0, pcur, pcur))));
       el(l, eb + i) = d;
       pm = pcur;
       pcur = pn;
@@ -315,7 +317,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
 #pragma unroll 4
     for (; i < nv; ++i) {
       const E pn = i + 1 < nv ? el(l, eb + i + 1) : right;
-      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmul(cinf.a0, pcur))));
+      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmad(cinf.a0, pcur, pcur))));
       el(l, eb + i) = d;
       pm = pcur;
       pcur = pn;
@@ -344,7 +346,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
     E b = sG[l2][k2], xx = sD[l2][k2];
 #pragma unroll
     for (int off = 1; off < kHS; off <<= 1) {
-      const E bn = shfl_down16(b, off), xn = shfl_down16(xx, off);
+      const E bn = shfl_down_seg(b, off), xn = shfl_down_seg(xx, off);
       if (k2 + off < kHS) {
         xx = cmad(b, xn, xx);
         b = cmul(b, bn);
@@ -368,7 +370,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
       for (int r = 7; r >= 0; --r)
         if (r > rank && r < cs) cin = cmad(rb[r], cin, rx[r]);
     }
-    const E bq = shfl_down16(b, 1), xq = shfl_down16(xx, 1);
+    const E bq = shfl_down_seg(b, 1), xq = shfl_down_seg(xx, 1);
     sD[l2][k2] = k2 == kHS - 1 ? cin : cmad(bq, cin, xq);
   }
   // every CTA's remote reads are done before any CTA moves on (and exits)

@@ -835,8 +835,10 @@ int run_steps(rotgp_ctx* c, long long n, bool imag) {
     for (int a = 0; a < c->grid.dim; ++a) {
       int rc;
       // the stencil and fused forms serve imaginary time; real-time steps
-      // keep the Thomas form, whose CN map stays unitary with rounded
-      // coefficients (the stencil's independently rounded weights do not)
+      // keep the folded Thomas form, whose near-unit diagonal factor is
+      // stored as its difference from 1 so that the rounded CN map stays
+      // unitary to ~1e-10 per sweep (the stencil's rounded central weight,
+      // close to 1 itself, would not)
       if (a == 0 && c->fuse_xy && imag) {
         rc = xy_pass(c, imag);
         ++a;  // the y sweep is part of the pass

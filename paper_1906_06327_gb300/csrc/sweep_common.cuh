@@ -107,12 +107,12 @@ __device__ __forceinline__ cpx<T> cfma(cpx<T> a, cpx<T> b, cpx<T> c) {
   return mk<T>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
-// One forward step d' = a0 pc + am pm + ap pn + al d', summed as two
+// One forward step d' = (1 + a0) pc + am pm + ap pn + al d', summed as two
 // independent halves so that only the last complex FMA waits on d'.
 template <class T>
 __device__ __forceinline__ cpx<T> fwd(const coef5<T>& k, cpx<T> pm, cpx<T> pc, cpx<T> pn,
                                       cpx<T> d) {
-  const cpx<T> s1 = cfma(k.am, pm, k.a0 * pc);
+  const cpx<T> s1 = cfma(k.am, pm, cfma(k.a0, pc, pc));
   const cpx<T> s2 = cfma(k.ap, pn, s1);
   return cfma(k.al, d, s2);
 }
@@ -257,10 +257,10 @@ __device__ __forceinline__ c2 kfma2(const k2& k, const c2& b, const c2& c) {
   r.im = __ffma2_rn(k.y, b.re, __ffma2_rn(k.x, b.im, c.im));
   return r;
 }
-// forward step of both lines: d' = a0 pc + am pm + ap pn + al d'
+// forward step of both lines: d' = (1 + a0) pc + am pm + ap pn + al d'
 __device__ __forceinline__ c2 fwd2(const coef2& k, const c2& pm, const c2& pc, const c2& pn,
                                    const c2& d) {
-  return kfma2(k.al, d, kfma2(k.ap, pn, kfma2(k.am, pm, kmul2(k.a0, pc))));
+  return kfma2(k.al, d, kfma2(k.ap, pn, kfma2(k.am, pm, kfma2(k.a0, pc, pc))));
 }
 __device__ __forceinline__ c2 zero2() {
   c2 r;

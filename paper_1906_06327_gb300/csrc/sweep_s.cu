@@ -22,7 +22,8 @@ namespace rotgp {
 // --------------------------------------------------------------- tables
 // Thomas multipliers of one line, m_1 = 1/A0, c'_1 = A+ m_1,
 // m_p = 1/(A0 - A- c'_{p-1}), c'_p = A+ m_p, folded into coef5 entries
-// p = 1..lt (computed in double); entry 0 is zero.
+// p = 1..lt (computed in double, a0 as its difference from 1); entry 0 is
+// zero.
 struct dcx {
   double x, y;
 };
@@ -52,7 +53,8 @@ __global__ void k_tables(coef5<T>* tab, float2* tabT, int nlines, int lt, axis_c
   for (int p = 1; p <= lt; ++p) {
     const dcx m = dinv(dsub(a0, dmul(am, c)));
     c = dmul(ap, m);
-    t[p].a0 = dcast<T>(dmul(m, diag));
+    const dcx md = dmul(m, diag);
+    t[p].a0 = dcast<T>({md.x - 1.0, md.y});
     t[p].am = dcast<T>(dmul(m, kmt));
     t[p].ap = dcast<T>(dmul(m, kpt));
     const dcx mam = dmul(m, am);

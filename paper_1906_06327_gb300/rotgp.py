@@ -558,13 +558,18 @@ class WarmStart:
     def propose(self, prm, half_width: float, seed=None) -> np.ndarray:
         """prm: (n, 3) array of (Omega, g, nu); returns n ABI wave functions
         ((G+1) x (G+1) complex128, edges zero, not normalised); with `seed`
-        multiplied by the random phase of Eq. fun drawn from that seed."""
-        prm, pp = self._prm(prm)
+        multiplied by the random phase of Eq. fun drawn from that seed.  More
+        than max_batch sets are proposed max_batch at a time (the phase
+        depends on the point only, not on the position in the batch)."""
+        prm = np.ascontiguousarray(prm, dtype=np.float64).reshape(-1, 3)
         n = prm.shape[0]
         out = np.zeros((n, self.grid + 1, self.grid + 1), dtype=np.complex128)
-        self._check(self._lib.rotgp_ws_propose(
-            self._h, n, pp, float(half_width), int(seed is not None),
-            int(seed or 0) & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(out.ctypes.data), 0))
+        for s in range(0, n, self.max_batch):
+            part, pp = self._prm(prm[s:s + self.max_batch])
+            dst = out[s:s + part.shape[0]]
+            self._check(self._lib.rotgp_ws_propose(
+                self._h, part.shape[0], pp, float(half_width), int(seed is not None),
+                int(seed or 0) & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(dst.ctypes.data), 0))
         return out
 
     def train_step(self, prm, half_width: float, psi, lr: float) -> float:

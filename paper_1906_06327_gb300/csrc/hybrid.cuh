@@ -200,8 +200,14 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   __syncthreads();
 
   // ---- H1 with the pending renormalisation (x sweep): psi <- s psi, then
-  // exp(-Delta (V + g|psi|^2)) or exp(-i Delta (V + g|psi|^2)) (Eq. eq1)
-  if (H1) {
+  // exp(-Delta (V + g|psi|^2)) or exp(-i Delta (V + g|psi|^2)) (Eq. eq1).
+  // Imaginary time advances the tile in place.  Real time leaves it as
+  // loaded: each forward pass forms every point as value + increment (hpt)
+  // when it reaches it.
+  constexpr bool RT = H1 && !IMAG;
+  const T h_s = (T)J.scale, h_gg = (T)a.g, h_dt = (T)a.dt;
+  const T h_hg2 = (T)a.hgam2, h_xs = (T)a.x0, h_hx = (T)a.hx;
+  if (H1 && IMAG) {
     const T s = (T)J.scale, hg2 = (T)a.hgam2, gg = (T)a.g, dt = (T)a.dt;
     const T xs = (T)a.x0, hx = (T)a.hx;
     for (int l = 0; l < kHL; ++l) {
@@ -211,14 +217,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
         const T x = fma((T)(p0 - 2 + e), hx, xs);
         E v = rscale(s, row[e]);
         const T en = fma(gg, sq(v), fma(hg2 * x, x, vyz));
-        if (IMAG) {
-          v = rscale(exp_t(-dt * en), v);
-        } else {
-          T c1, s1;
-          rot_t(dt * en, &c1, &s1);
-          v = mk<T>(fma(c1, v.x, fma(s1, v.y, v.x)), fma(c1, v.y, fma(-s1, v.x, v.y)));
-        }
-        row[e] = v;
+        row[e] = rscale(exp_t(-dt * en), v);
       }
     }
     __syncthreads();
@@ -239,16 +238,50 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   // the scan threads: a warp over the sub-segments of one line
   const int l2 = tid / kHS, k2 = tid % kHS;
 
+  // real time: the loaded value u of tile position e of this thread's line,
+  // scaled and advanced
+  auto rt_at = [&](E u, int e) -> hpt<T> {
+    const T x = fma((T)(p0 - 2 + e), h_hx, h_xs);
+    const E v = rscale(h_s, u);
+    const T en = fma(h_gg, sq(v), fma(h_hg2 * x, x, hv[AX == 0 ? l : 0]));
+    T c1, s1;
+    rot_t(h_dt * en, &c1, &s1);
+    return rot_inc(v, c1, s1);
+  };
+  auto rt = [&](int e) -> hpt<T> { return rt_at(el(l, e), e); };
+
   // ---- F1: local forward from a zero carry; summary (prod al, d at the end)
   const E left = el(l, eb - 1), right = el(l, eb + nv);
-  {
+  if constexpr (RT) {
+    E d = zero<T>(), G = mk<T>(1, 0);
+    E pm = hw(rt_at(left, eb - 1));
+    hpt<T> pc = rt(eb);
+    int i = 0;
+    for (; i < it; ++i) {
+      const hpt<T> pn = i + 1 < nv ? rt(eb + i + 1) : rt_at(right, eb + nv);
+      d = fwd_inc(crow[pb + i], pm, pc, hw(pn), d);
+      G = cmul(crow[pb + i].al, G);
+      pm = hw(pc);
+      pc = pn;
+    }
+#pragma unroll 2
+    for (; i < nv; ++i) {
+      const hpt<T> pn = i + 1 < nv ? rt(eb + i + 1) : rt_at(right, eb + nv);
+      d = fwd_inc(cinf, pm, pc, hw(pn), d);
+      pm = hw(pc);
+      pc = pn;
+    }
+    if (nv > it) G = cmul(G, cpow_n(cinf.al, nv - it));
+    sG[l][k] = G;
+    sD[l][k] = d;
+  } else {
     E d = zero<T>(), G = mk<T>(1, 0);
     E pm = left, pcur = el(l, eb);
     int i = 0;
     for (; i < it; ++i) {
       const coef5<T> c = crow[pb + i];
       const E pn = el(l, eb + i + 1);
-      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmad(c.a0, pcur, pcur))));
+      d = fwd(c, pm, pcur, pn, d);
       G = cmul(c.al, G);
       pm = pcur;
       pcur = pn;
@@ -256,7 +289,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
 #pragma unroll 4
     for (; i < nv; ++i) {
       const E pn = el(l, eb + i + 1);
-      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmad(cinf.a0, pcur, pcur))));
+      d = fwd(cinf, pm, pcur, pn, d);
       pm = pcur;
       pcur = pn;
     }
@@ -302,14 +335,38 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   __syncthreads();
 
   // ---- F2: forward from the true carry; d overwrites psi in the tile
-  {
+  if constexpr (RT) {
+    // the neighbours outside the sub-segment come from the values read
+    // before the barrier: the adjacent sub-segments overwrite them in this
+    // pass (inside it, the read of eb + i + 1 precedes the store at eb + i + 1)
+    E d = sD[l][k];
+    E pm = hw(rt_at(left, eb - 1));
+    hpt<T> pc = rt(eb);
+    const hpt<T> rend = rt_at(right, eb + nv);
+    int i = 0;
+    for (; i < it; ++i) {
+      const hpt<T> pn = i + 1 < nv ? rt(eb + i + 1) : rend;
+      d = fwd_inc(crow[pb + i], pm, pc, hw(pn), d);
+      el(l, eb + i) = d;
+      pm = hw(pc);
+      pc = pn;
+    }
+#pragma unroll 2
+    for (; i < nv; ++i) {
+      const hpt<T> pn = i + 1 < nv ? rt(eb + i + 1) : rend;
+      d = fwd_inc(cinf, pm, pc, hw(pn), d);
+      el(l, eb + i) = d;
+      pm = hw(pc);
+      pc = pn;
+    }
+  } else {
     E d = sD[l][k];
     E pm = left, pcur = el(l, eb);
     int i = 0;
     for (; i < it; ++i) {
       const coef5<T> c = crow[pb + i];
       const E pn = i + 1 < nv ? el(l, eb + i + 1) : right;
-      d = cmad(c.al, d, cmad(c.ap, pn, cmad(c.am, pm, cmad(c.a0, pcur, pcur))));
+      d = fwd(c, pm, pcur, pn, d);
       el(l, eb + i) = d;
       pm = pcur;
       pcur = pn;
@@ -317,7 +374,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
 #pragma unroll 4
     for (; i < nv; ++i) {
       const E pn = i + 1 < nv ? el(l, eb + i + 1) : right;
-      d = cmad(cinf.al, d, cmad(cinf.ap, pn, cmad(cinf.am, pm, cmad(cinf.a0, pcur, pcur))));
+      d = fwd(cinf, pm, pcur, pn, d);
       el(l, eb + i) = d;
       pm = pcur;
       pcur = pn;
@@ -328,11 +385,11 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
     E x = zero<T>(), B = mk<T>(1, 0);
     int i = nv - 1;
 #pragma unroll 4
-    for (; i >= it; --i) x = cmad(cinf.be, x, el(l, eb + i));
+    for (; i >= it; --i) x = bwd(cinf.be, x, el(l, eb + i));
     if (nv > it) B = cpow_n(cinf.be, nv - it);
     for (; i >= 0; --i) {
       const coef5<T> c = crow[pb + i];
-      x = cmad(c.be, x, el(l, eb + i));
+      x = bwd(c.be, x, el(l, eb + i));
       B = cmul(c.be, B);
     }
     __syncthreads();  // every thread has read its forward carry
@@ -383,13 +440,13 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
     int i = nv - 1;
 #pragma unroll 4
     for (; i >= it; --i) {
-      x = cmad(cinf.be, x, el(l, eb + i));
+      x = bwd(cinf.be, x, el(l, eb + i));
       el(l, eb + i) = x;
       if (REDUCE) acc.add(sq(x));
     }
     for (; i >= 0; --i) {
       const coef5<T> c = crow[pb + i];
-      x = cmad(c.be, x, el(l, eb + i));
+      x = bwd(c.be, x, el(l, eb + i));
       el(l, eb + i) = x;
       if (REDUCE) acc.add(sq(x));
     }

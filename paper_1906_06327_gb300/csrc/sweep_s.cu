@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128) k_sweep_strided(const stream_args a) {
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             const E be = crow[v][min(q * C + h, lt)].be;
-            x[v] = cfma(be, x[v], t.v[v]);
+            x[v] = bwd(be, x[v], t.v[v]);
           }
         }
         const Pk* sp = slot(qq);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(128) k_sweep_strided(const stream_args a) {
             Pk o;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-              x[v] = cfma(coef_at<T, FAST>(crow[v], cinf[v], p, lt).be, x[v], t.v[v]);
+              x[v] = bwd(coef_at<T, FAST>(crow[v], cinf[v], p, lt).be, x[v], t.v[v]);
               o.v[v] = x[v];
               if (REDUCE) acc.add(abs2(x[v]));
             }
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(128) k_sweep_strided2(const stream_args a) {
             const int i = min(q * C + h, lt);
             be = make_k2(crow[0][i].be, crow[1][i].be);
           }
-          x = kfma2(be, x, unpack_split(sq[h * 32]));
+          x = bwd2(be, x, unpack_split(sq[h * 32]));
         }
         const float4* sp = slot(qq);
         const bool fast = qq * C >= lt && q * C <= N;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(128) k_sweep_strided2(const stream_args a) {
               const int i = min(p, lt);
               be = make_k2(crow[0][i].be, crow[1][i].be);
             }
-            x = kfma2(be, x, unpack_split(w[r]));
+            x = bwd2(be, x, unpack_split(w[r]));
             if (REDUCE) {
               const float2 n2 = __ffma2_rn(x.im, x.im, __fmul2_rn(x.re, x.re));
               acc.add(n2.x + n2.y);

@@ -118,9 +118,61 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
       rp[2 * k + 1] = e1;
     }
   };
+  // real time: psi at position p scaled and held as value + H1 increment
+  auto h1p = [&](E psi, int p, int v) -> hpt<T> {
+    psi = s * psi;
+    const T x = xs + (T)p * hx;
+    const T en = hg2 * x * x + vyz[v] + gg * abs2(psi);
+    T c1, s1;
+    rot_t(dt * en, &c1, &s1);
+    return rot_inc(psi, c1, s1);
+  };
+  // real-time forward sweep over one chunk (the centre point of every step
+  // enters as value + increment, fwd_inc)
+  auto forward_rt = [&](auto fast_tag, E* s0, int p0, E (&pm)[V], E (&d)[V]) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    hpt<T> c0[V], c1[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      E r0, r1;
+      load2(s0 + (lane + 32 * v) * PITCH, 0, r0, r1);
+      c0[v] = h1p(r0, p0, v);
+      c1[v] = h1p(r1, p0 + 1, v);
+    }
+#pragma unroll(unroll_of<C / 2>::value)
+    for (int k = 0; k < C / 2; ++k) {
+      const int p = p0 + 2 * k;
+      hpt<T> n0[V], n1[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (k + 1 < C / 2) {
+          E r0, r1;
+          load2(s0 + (lane + 32 * v) * PITCH, k + 1, r0, r1);
+          n0[v] = h1p(r0, p + 2, v);
+          n1[v] = h1p(r1, p + 3, v);
+        } else {
+          n0[v] = h1p(s0[(lane + 32 * v) * PITCH + C], p + 2, v);
+          n1[v] = {zero<T>(), zero<T>()};
+        }
+        const E w1 = hw(c1[v]);
+        d[v] = fwd_inc(coef_at<T, FAST>(crow[v], cinf[v], p, lt), pm[v], c0[v], w1, d[v]);
+        const E e0 = d[v];
+        d[v] = fwd_inc(coef_at<T, FAST>(crow[v], cinf[v], p + 1, lt), hw(c0[v]), c1[v],
+                       hw(n0[v]), d[v]);
+        store2(s0 + (lane + 32 * v) * PITCH, k, e0, d[v]);
+        pm[v] = w1;
+        c0[v] = n0[v];
+        c1[v] = n1[v];
+      }
+    }
+  };
   // forward sweep over one chunk of the lane's V rows (psi -> d' in place)
   auto forward = [&](auto fast_tag, E* s0, int p0, E (&pm)[V], E (&d)[V]) {
     constexpr bool FAST = decltype(fast_tag)::value;
+    if constexpr (!IMAG) {
+      forward_rt(fast_tag, s0, p0, pm, d);
+      return;
+    }
     E c0[V], c1[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -162,9 +214,9 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
       for (int v = 0; v < V; ++v) {
         E d0, d1;
         load2(sp + (lane + 32 * v) * PITCH, k, d0, d1);
-        if (FAST || p + 1 < N) x[v] = cfma(coef_at<T, FAST>(crow[v], cinf[v], p + 1, lt).be, x[v], d1);
+        if (FAST || p + 1 < N) x[v] = bwd(coef_at<T, FAST>(crow[v], cinf[v], p + 1, lt).be, x[v], d1);
         const E e1 = x[v];
-        if (FAST || p < N) x[v] = cfma(coef_at<T, FAST>(crow[v], cinf[v], p, lt).be, x[v], d0);
+        if (FAST || p < N) x[v] = bwd(coef_at<T, FAST>(crow[v], cinf[v], p, lt).be, x[v], d0);
         store2(sp + (lane + 32 * v) * PITCH, k, x[v], e1);
       }
     }
@@ -194,7 +246,7 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const E be = crow[v][min(q * C + h, lt)].be;
-          x[v] = cfma(be, x[v], sq[(lane + 32 * v) * PITCH + h]);
+          x[v] = bwd(be, x[v], sq[(lane + 32 * v) * PITCH + h]);
         }
       }
       E* sp = slot(qq);
@@ -303,15 +355,24 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
       const float2 f = make_float2(__expf(-dt * en.x), __expf(-dt * en.y));
       v.re = __fmul2_rn(f, v.re);
       v.im = __fmul2_rn(f, v.im);
-    } else {
-      float2 s1, c1;
-      rot_t(dt * en.x, &c1.x, &s1.x);
-      rot_t(dt * en.y, &c1.y, &s1.y);
-      const float2 re = __ffma2_rn(c1, v.re, __ffma2_rn(s1, v.im, v.re));
-      v.im = __ffma2_rn(c1, v.im, __ffma2_rn(make_float2(-s1.x, -s1.y), v.re, v.im));
-      v.re = re;
     }
     return v;
+  };
+  // real time: both rows' psi at p scaled, and the H1 increment dl (see hpt)
+  auto h1_inc = [&](c2& v, int p) -> c2 {
+    v.re = __fmul2_rn(S2, v.re);
+    v.im = __fmul2_rn(S2, v.im);
+    const float x = xs + (float)p * hx;
+    const float vx = hg2 * x * x;
+    const float2 dens = __ffma2_rn(v.im, v.im, __fmul2_rn(v.re, v.re));
+    const float2 en = __ffma2_rn(G2, dens, __fadd2_rn(VYZ, make_float2(vx, vx)));
+    float2 s1, c1;
+    rot_t(dt * en.x, &c1.x, &s1.x);
+    rot_t(dt * en.y, &c1.y, &s1.y);
+    c2 dl;
+    dl.re = __ffma2_rn(c1, v.re, __fmul2_rn(s1, v.im));
+    dl.im = __ffma2_rn(c1, v.im, __fmul2_rn(make_float2(-s1.x, -s1.y), v.re));
+    return dl;
   };
   auto slot = [&](int q) { return ring + (size_t)((q - qa) % R) * SLOT; };
   auto issue = [&](int q) {
@@ -368,14 +429,33 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
     for (int k = 0; k < C / 2; ++k) load_pair(s0, k, w[2 * k], w[2 * k + 1]);
     w[C].re = make_float2(s0[lane * PITCH + C].x, s0[(lane + 32) * PITCH + C].x);
     w[C].im = make_float2(s0[lane * PITCH + C].y, s0[(lane + 32) * PITCH + C].y);
+    if (IMAG) {
 #pragma unroll
-    for (int r = 0; r <= C; ++r) w[r] = h1(w[r], p0 + r);
+      for (int r = 0; r <= C; ++r) w[r] = h1(w[r], p0 + r);
 #pragma unroll
-    for (int r = 0; r < C; ++r) {
-      const c2 pc = w[r];
-      d = fwd2(coef_p(fast_tag, p0 + r), pm, pc, w[r + 1], d);
-      pm = pc;
-      w[r] = d;
+      for (int r = 0; r < C; ++r) {
+        const c2 pc = w[r];
+        d = fwd2(coef_p(fast_tag, p0 + r), pm, pc, w[r + 1], d);
+        pm = pc;
+        w[r] = d;
+      }
+    } else {
+      // the centre point as value + increment, its neighbours rounded
+      c2 dl = h1_inc(w[0], p0);
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        const c2 dn = h1_inc(w[r + 1], p0 + r + 1);
+        c2 pn;
+        pn.re = __fadd2_rn(w[r + 1].re, dn.re);
+        pn.im = __fadd2_rn(w[r + 1].im, dn.im);
+        c2 pc;
+        pc.re = __fadd2_rn(w[r].re, dl.re);
+        pc.im = __fadd2_rn(w[r].im, dl.im);
+        d = fwd2_inc(coef_p(fast_tag, p0 + r), pm, w[r], dl, pn, d);
+        pm = pc;
+        w[r] = d;
+        dl = dn;
+      }
     }
 #pragma unroll
     for (int k = 0; k < C / 2; ++k) store_pair(s0, k, w[2 * k], w[2 * k + 1]);
@@ -388,7 +468,7 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
     for (int k = 0; k < C / 2; ++k) load_pair(sp, k, w[2 * k], w[2 * k + 1]);
 #pragma unroll
     for (int r = C - 1; r >= 0; --r) {
-      if (FAST || p0 + r < N) x = kfma2(coef_p(fast_tag, p0 + r).be, x, w[r]);
+      if (FAST || p0 + r < N) x = bwd2(coef_p(fast_tag, p0 + r).be, x, w[r]);
       w[r] = x;
     }
 #pragma unroll
@@ -441,7 +521,7 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
         c2 t;
         t.re = make_float2(sq[lane * PITCH + h].x, sq[(lane + 32) * PITCH + h].x);
         t.im = make_float2(sq[lane * PITCH + h].y, sq[(lane + 32) * PITCH + h].y);
-        x = kfma2(be, x, t);
+        x = bwd2(be, x, t);
       }
       E* sp = slot(qq);
       if (qq * C >= lt && q * C <= N)
@@ -480,9 +560,13 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
 // z_p = d_p + be z_{p+1}; psi'_p = z_p - psi_p, psi after H1), keeps the
 // H1-advanced points in the slot for the back substitution one chunk later,
 // overwrites them with the results, and the slot leaves as one TMA box
-// store.  Ring of R + 1 slots as in k_sweep_s1t.
+// store.  Ring of R + 1 slots as in k_sweep_s1t.  Registers are capped so
+// that a full SM of warps stays resident: 16 warps x 128 for C = 8, 14 warps
+// x 144 (64,512 of the SM's 65,536) for C = 16, whose ring of R = 3 then
+// also fits (14 x 16 KB of shared memory) -- one wave of 32-row units on the
+// 512 x 512 x 128 state instead of 1.7 waves of 8 warps per SM.
 template <int C, bool IMAG, int RING>
-__global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
+__global__ void __maxnreg__(C == 8 ? 128 : 144) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
                                                    const __grid_constant__ CUtensorMap omap,
                                                    const stream_args a) {
   constexpr int NS = RING + 1;        // slots per warp
@@ -493,7 +577,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[16 * 8];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.ring != RING || blockDim.x > (C == 8 ? 512u : 256u) ||
+  if (a.ring != RING || blockDim.x > (C == 8 ? 512u : 448u) ||
       dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(NS * SLOT * 8) + 1024u) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
@@ -753,7 +837,7 @@ static cudaError_t dispatch_x1t(bool imag, const stream_args& a, const sweep_sha
   const long long units = (a.nlines + 31) / 32 * a.nseg;
   int W = 1;
   unsigned blocks = 0;
-  e = resident_grid((const void*)fn, units, x1t_smem_per_warp(C, R), 1024, C == 8 ? 16 : 8, &W,
+  e = resident_grid((const void*)fn, units, x1t_smem_per_warp(C, R), 1024, C == 8 ? 16 : 14, &W,
                     &blocks);
   if (e != cudaSuccess) return e;
   return launch_programmatic(fn, blocks, 32 * W, x1t_smem_per_warp(C, R) * W + 1024, s, m, om, a);

@@ -13,7 +13,9 @@ and |G(k)| = 1 for every k in exact arithmetic (the CN map of a Hermitian
 operator is unitary).  The complex-float kernels use the coefficients rounded
 to float; |G(k)|^2 - 1 of the rounded values bounds the norm change of one
 sweep.  Kept as a0 = m (1 - 2 kappa) - 1, the rounding of the diagonal factor
-no longer dominates.
+no longer dominates.  (The rounding of the arithmetic itself is a separate,
+smaller effect: see the summation order of the folded recurrences in the
+kernels.)
 """
 import numpy as np
 

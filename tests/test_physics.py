@@ -115,15 +115,23 @@ def test_table1_2d_lattices_37_and_61_vortices(lattices_ab):
 # k and every x or y line of the h = 0.05, Delta = 1e-4 grids (Omega = 0.8)
 # and below 4.0e-9 for the z lines of the 3D disk (h = 0.025).  One 2D step
 # (two sweeps) thus moves the norm by at most 7.2e-9 and one 3D step by
-# 1.12e-8; the state-weighted average over lines is far smaller.
+# 1.12e-8 through the coefficients; on smooth states and vortex lattices the
+# spectrum-weighted value is ~1e-11.  The arithmetic adds a rounding bias of
+# its own, which the kernels keep near 1e-10 per step: the H1 rotation is
+# carried into the x sweep as an increment, and every recurrence step sums
+# its small terms before adding the large one.  The tests hold the runs to
+# the coefficient bound and, tighter, to the level the arithmetic leaves
+# (ARITH_PER_STEP; measured on GB300: -3e-12 per step on lattice (a), 3e-10
+# on the 3D disk).
 NORM_PER_STEP_2D = 7.2e-9
 NORM_PER_STEP_3D = 1.12e-8
+ARITH_PER_STEP = 1e-9
 
 
 def test_real_time_500_time_units_keep_lattice_a(lattices_ab):
     """Fig. 2(e): 500 time units of real time from lattice (a) (5,000,000
     steps of 1e-4, complex float).  The lattice keeps its 7 vortices, the
-    norm stays within the bound that the rounded CN coefficients allow, and
+    norm stays within the bounds above (measured: -1.6e-5 over the run), and
     the energy per norm is conserved."""
     psi_a, oa = lattices_ab[0]
     s = Solver((256, 256), (0.05, 0.05), gamma=1.0, nu=1.0, g=100.0, omega=0.8, dt=1e-4)
@@ -137,6 +145,7 @@ def test_real_time_500_time_units_keep_lattice_a(lattices_ab):
     assert o1["vortices"] == 7, o1
     drift = norms[-1] - norms[0]
     assert abs(drift) < NORM_PER_STEP_2D * 5_000_000, norms
+    assert abs(drift) < ARITH_PER_STEP * 5_000_000, norms
     assert abs(o1["energy4"] / o1["norm"] - o0["energy4"] / o0["norm"]) < 5e-3 * o0["energy4"]
     print(f"500 time units of real time: norm {norms[0]:.9f} -> {norms[1]:.9f} -> "
           f"{norms[2]:.9f} (drift {drift:.2e}), energy4 {o0['energy4']:.5f} -> "
@@ -175,6 +184,7 @@ def test_table1_3d_lattice_and_reduced_density(lattices_ab):
     o1 = s.observables()
     assert o1["vortices"] == int(vort_ref), o1
     assert abs(o1["norm"] - n0) < NORM_PER_STEP_3D * 1_000_000, (n0, o1["norm"])
+    assert abs(o1["norm"] - n0) < ARITH_PER_STEP * 1_000_000, (n0, o1["norm"])
     N = col0.shape[0]
     c = (N - 1) / 2
     yy, xx = np.mgrid[0:N, 0:N]

@@ -560,13 +560,12 @@ __global__ void __launch_bounds__(128) k_sweep_x2(const __grid_constant__ CUtens
 // z_p = d_p + be z_{p+1}; psi'_p = z_p - psi_p, psi after H1), keeps the
 // H1-advanced points in the slot for the back substitution one chunk later,
 // overwrites them with the results, and the slot leaves as one TMA box
-// store.  Ring of R + 1 slots as in k_sweep_s1t.  Registers are capped so
-// that a full SM of warps stays resident: 16 warps x 128 for C = 8, 14 warps
-// x 144 (64,512 of the SM's 65,536) for C = 16, whose ring of R = 3 then
-// also fits (14 x 16 KB of shared memory) -- one wave of 32-row units on the
-// 512 x 512 x 128 state instead of 1.7 waves of 8 warps per SM.
+// store.  Ring of R + 1 slots as in k_sweep_s1t.  C = 16 runs 8 warps per
+// SM with all the registers it wants (166); capped at 144 so that 14 warps
+// fit (one wave of units on the 512 x 512 x 128 state) it measured slower
+// on GB300 (141 against 114 us per sweep).
 template <int C, bool IMAG, int RING>
-__global__ void __maxnreg__(C == 8 ? 128 : 144) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_constant__ CUtensorMap map,
                                                    const __grid_constant__ CUtensorMap omap,
                                                    const stream_args a) {
   constexpr int NS = RING + 1;        // slots per warp
@@ -577,7 +576,7 @@ __global__ void __maxnreg__(C == 8 ? 128 : 144) k_sweep_x1t(const __grid_constan
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[16 * 8];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (a.ring != RING || blockDim.x > (C == 8 ? 512u : 448u) ||
+  if (a.ring != RING || blockDim.x > (C == 8 ? 512u : 256u) ||
       dynamic_smem_bytes() < (blockDim.x >> 5) * (unsigned)(NS * SLOT * 8) + 1024u) {
     if (threadIdx.x == 0) atomicOr(a.flags, 2);
     return;
@@ -837,7 +836,7 @@ static cudaError_t dispatch_x1t(bool imag, const stream_args& a, const sweep_sha
   const long long units = (a.nlines + 31) / 32 * a.nseg;
   int W = 1;
   unsigned blocks = 0;
-  e = resident_grid((const void*)fn, units, x1t_smem_per_warp(C, R), 1024, C == 8 ? 16 : 14, &W,
+  e = resident_grid((const void*)fn, units, x1t_smem_per_warp(C, R), 1024, C == 8 ? 16 : 8, &W,
                     &blocks);
   if (e != cudaSuccess) return e;
   return launch_programmatic(fn, blocks, 32 * W, x1t_smem_per_warp(C, R) * W + 1024, s, m, om, a);

@@ -19,18 +19,20 @@
 // the true carries.  Nothing is truncated: the result is the Thomas solution
 // of the whole line up to rounding, whatever the decay of the carries.
 //
-// Layout.  A CTA of 512 threads holds a tile of 16 lines x pc positions (+2
+// Layout.  A CTA of 256 threads holds a tile of 16 lines x pc positions (+2
 // halo positions either side) in shared memory; thread (line l, sub-segment
-// k) owns lsub = pc/32 consecutive positions of line l.  A line longer than
+// k) owns lsub = pc/16 consecutive positions of line l.  A line longer than
 // one tile is spread over a cluster of cs CTAs (cs = 1, 2, 4 or 8), CTA r
 // holding positions [r pc, (r+1) pc); the CTAs exchange their per-line
 // summaries through distributed shared memory.  x lines (contiguous rows) sit
 // in the tile as [line][position] with an even pitch and an odd lsub, so the
-// 32 threads of a warp (the 32 sub-segments of one line) touch every bank
-// pair twice; y and z lines (16 consecutive x at one transverse position, 128
-// contiguous bytes per position in complex float) sit as [position][line], a
-// warp being 16 lines x 2 sub-segments.  The affine scans over a line's
-// sub-segments run in one warp with shuffles.  Each point is read from and written to global
+// 32 threads of a warp (2 lines x 16 sub-segments) touch distinct banks; y
+// and z lines (16 consecutive x at one transverse position, 128 contiguous
+// bytes per position in complex float) sit as [position][line], a warp being
+// 16 lines x 2 sub-segments.  The affine scans over a line's sub-segments run
+// in a half-warp with shuffles (32 sub-segments per line in a full warp
+// measured slower on GB300: 3.0e10 against 3.3e10 site-updates/s on the 4096^2
+// state, 241 against 196 us per persistent batch step).  Each point is read from and written to global
 // memory once per sweep; H1 (with the pending renormalisation) is applied to
 // the tile as it lands in the x sweep; the last sweep of a step reduces the
 // norm.  The same kernel serves both propagation modes (the table of the mode

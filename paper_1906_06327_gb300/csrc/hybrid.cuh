@@ -14,8 +14,8 @@ namespace rotgp {
 namespace hyb {
 
 constexpr int kHL = 16;                 // lines per tile
-constexpr int kHS = 32;                 // sub-segments per line in one CTA (a warp)
-constexpr int kHThreads = kHL * kHS;    // 512
+constexpr int kHS = 16;                 // sub-segments per line in one CTA (a half-warp)
+constexpr int kHThreads = kHL * kHS;    // 256
 
 template <class T>
 __device__ __forceinline__ cpx<T> cmad(cpx<T> a, cpx<T> b, cpx<T> c) {
@@ -235,7 +235,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   if (AX == 1) li = line_ok(l) ? x0l + l : 0;
   const coef5<T>* crow = static_cast<const coef5<T>*>(a.coef) + (size_t)li * (lt + 1);
   const coef5<T> cinf = crow[lt];
-  // the scan threads: a warp over the sub-segments of one line
+  // the scan threads: a half-warp over the sub-segments of one line
   const int l2 = tid / kHS, k2 = tid % kHS;
 
   // real time: the loaded value u of tile position e of this thread's line,
@@ -299,7 +299,7 @@ __device__ __forceinline__ double hybrid_tile(const stream_args& a, const hybrid
   }
   __syncthreads();
   // reduced system, forward: affine prefix over the sub-segments of a line
-  // (log-depth scan in a warp), the CTA total to the cluster, and the true d
+  // (log-depth scan in a half-warp), the CTA total to the cluster, and the true d
   // before every sub-segment
   {
     E g = sG[l2][k2], dd = sD[l2][k2];

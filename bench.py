@@ -338,8 +338,11 @@ def _roofline(kstats: dict, peak: float, peak_kind: str, workload: str, plan: st
     avg_ms = drec["total_ms"] / drec["launches"]
     achieved = drec["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
     tot = max(1e-9, sum(x["total_ms"] for x in kstats.values()))
+    traffic = _traffic(dname, workload, plan)
     return {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": _traffic(dname, workload, plan),
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            # DRAM bytes (ncu, per launch) over the same mean launch time
+            "dram_achieved": traffic / (avg_ms * 1e-3) / 1e9 if traffic else None,
             "peak_source": peak_kind, "workload": workload, "plan": plan,
             "algorithmic_bytes_per_launch": drec["bytes_per_launch"],
             "avg_launch_ms": avg_ms,

@@ -308,7 +308,7 @@ def run_reference(a, w):
 # launches that the committed ncu records describe.
 PLANS = {
     "3d-256x256x128-fp32": "thomas:1,8,6,2/thomas:1,8,5,2/thomas:1,8,4,1",
-    "3d-512x512x128-fp32": "thomas:1,16,4,1/thomas:1,8,3,1/thomas:1,8,3,1",
+    "3d-512x512x128-fp32": "thomas:1,8,5,2/thomas:1,8,3,1/thomas:1,8,3,1",
 }
 
 

@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
   // and visible past this wait, and nothing above touched global memory
   griddep_launch_dependents();
   griddep_wait();
-  const uint64_t pol_first = l2_evict_first(), pol_last = l2_evict_last();
+  const uint64_t pol_last = l2_evict_last();
   unsigned ph = 0;  // phase parity of every slot's barrier, kept from unit to unit
   bool good = true;
   // units (32 rows and one segment of them) in a fixed round-robin order
@@ -667,11 +667,14 @@ __global__ void __launch_bounds__(C == 8 ? 512 : 256) k_sweep_x1t(const __grid_c
     auto unit = [&](int sl, int u) -> float4* {
       return reinterpret_cast<float4*>(ring + (size_t)sl * SLOT + lane * C) + (u ^ swz);
     };
+    // the row pieces of a box (64 or 128 bytes of each of 32 rows) are loaded
+    // with the normal L2 policy: with evict_first the rest of the lines they
+    // share with the next chunk left L2 before that chunk's load, and on a
+    // state larger than L2 the sweep read 14-43% of the state twice from DRAM
     auto issue = [&](int q, int sl) {  // lane 0
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(&bar[sl], (unsigned)(SLOT * 8));
-      tma_load_2d_hint(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl],
-                       pol_first);
+      tma_load_2d(ring + (size_t)sl * SLOT, &map, 2 * q * C, (int)row0, &bar[sl]);
     };
     if (lane == 0) {
       bulk_wait_read<0>();  // the previous unit's stores have left their slots

@@ -90,10 +90,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// L2 cache policies for loads: evict_first for data read once (the state a
-// sweep streams through, so that it does not push the sweep's output, read
-// by the next sweep, out of L2), evict_last for small tables read by every
-// sweep.
+// L2 cache policies for loads: evict_first for data read once in whole
+// lines (the state the y and z sweeps stream through, so that it does not
+// push the sweep's output, read by the next sweep, out of L2), evict_last
+// for small tables read by every sweep.  The row (x) sweep's boxes read
+// parts of lines and keep the normal policy.
 __device__ __forceinline__ uint64_t l2_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));

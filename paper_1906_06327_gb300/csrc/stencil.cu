@@ -123,7 +123,7 @@ template <int K, bool IMAG>
 __global__ void __launch_bounds__(128) k_stencil_x(const stream_args a) {
   using E = cpx<float>;
   using LY = xstencil_layout<K>;
-  constexpr int S = 2 * K + 1, TW = LY::TW, WIN = LY::WIN, SP = LY::SP;
+  constexpr int S = 2 * K + 1, TW = LY::TW, SP = LY::SP;
   __shared__ float4 stage[4][SP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nrows = (int)a.nlines;

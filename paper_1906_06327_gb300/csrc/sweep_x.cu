@@ -168,39 +168,39 @@ __global__ void __launch_bounds__(128) k_sweep_x(const stream_args a) {
   };
   // forward sweep over one chunk of the lane's V rows (psi -> d' in place)
   auto forward = [&](auto fast_tag, E* s0, int p0, E (&pm)[V], E (&d)[V]) {
-    constexpr bool FAST = decltype(fast_tag)::value;
     if constexpr (!IMAG) {
       forward_rt(fast_tag, s0, p0, pm, d);
-      return;
-    }
-    E c0[V], c1[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      load2(s0 + (lane + 32 * v) * PITCH, 0, c0[v], c1[v]);
-      c0[v] = h1(c0[v], p0, v);
-      c1[v] = h1(c1[v], p0 + 1, v);
-    }
-#pragma unroll(unroll_of<C / 2>::value)
-    for (int k = 0; k < C / 2; ++k) {
-      const int p = p0 + 2 * k;
-      E n0[V], n1[V];
+    } else {
+      constexpr bool FAST = decltype(fast_tag)::value;
+      E c0[V], c1[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        if (k + 1 < C / 2) {
-          load2(s0 + (lane + 32 * v) * PITCH, k + 1, n0[v], n1[v]);
-          n0[v] = h1(n0[v], p + 2, v);
-          n1[v] = h1(n1[v], p + 3, v);
-        } else {
-          n0[v] = h1(s0[(lane + 32 * v) * PITCH + C], p + 2, v);
-          n1[v] = zero<T>();
+        load2(s0 + (lane + 32 * v) * PITCH, 0, c0[v], c1[v]);
+        c0[v] = h1(c0[v], p0, v);
+        c1[v] = h1(c1[v], p0 + 1, v);
+      }
+#pragma unroll(unroll_of<C / 2>::value)
+      for (int k = 0; k < C / 2; ++k) {
+        const int p = p0 + 2 * k;
+        E n0[V], n1[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          if (k + 1 < C / 2) {
+            load2(s0 + (lane + 32 * v) * PITCH, k + 1, n0[v], n1[v]);
+            n0[v] = h1(n0[v], p + 2, v);
+            n1[v] = h1(n1[v], p + 3, v);
+          } else {
+            n0[v] = h1(s0[(lane + 32 * v) * PITCH + C], p + 2, v);
+            n1[v] = zero<T>();
+          }
+          d[v] = fwd(coef_at<T, FAST>(crow[v], cinf[v], p, lt), pm[v], c0[v], c1[v], d[v]);
+          const E e0 = d[v];
+          d[v] = fwd(coef_at<T, FAST>(crow[v], cinf[v], p + 1, lt), c0[v], c1[v], n0[v], d[v]);
+          store2(s0 + (lane + 32 * v) * PITCH, k, e0, d[v]);
+          pm[v] = c1[v];
+          c0[v] = n0[v];
+          c1[v] = n1[v];
         }
-        d[v] = fwd(coef_at<T, FAST>(crow[v], cinf[v], p, lt), pm[v], c0[v], c1[v], d[v]);
-        const E e0 = d[v];
-        d[v] = fwd(coef_at<T, FAST>(crow[v], cinf[v], p + 1, lt), c0[v], c1[v], n0[v], d[v]);
-        store2(s0 + (lane + 32 * v) * PITCH, k, e0, d[v]);
-        pm[v] = c1[v];
-        c0[v] = n0[v];
-        c1[v] = n1[v];
       }
     }
   };
@@ -856,7 +856,6 @@ static cudaError_t dispatch_x2r(bool imag, bool vec16, const stream_args& a,
                           : k_sweep_x2<C, false, true, false, R>)
                   : (imag ? k_sweep_x2<C, true, false, false, R>
                           : k_sweep_x2<C, false, false, false, R>);
-  const int k = (tma ? 4 : vec16 ? 2 : 0) + (imag ? 1 : 0);
   cudaError_t e = allow_smem((const void*)fn);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)sh.blocks, 32 * sh.warps_per_block, sh.smem + (tma ? 128 : 0), s>>>(m, a);
